@@ -1,0 +1,498 @@
+"""Benchmark: bulk incremental connectivity on one GB300 (or N replicas).
+
+Workload (default ``rmat``): one forest on n = 2^24 vertices fed by 2^27
+R-MAT edges (a, b, c, d = 0.57, 0.19, 0.19, 0.05, ids randomly permuted,
+seed = rank) in 128 minibatches of 2^20 edges; after each Bulk-Update, one
+Bulk-Query of 2^20 uniform vertex pairs. A STEP is one minibatch of that
+stream: the Bulk-Update, its compression pass and the Bulk-Query. Step i
+processes minibatch i mod 128; at each wrap the forest is reset to n
+singletons inside the step, so every pass starts from the empty graph.
+
+Timing: W warm-up steps on a separate pass, reset, then exactly K steps
+bracketed by a barrier and a device synchronise, timed with CUDA events on
+the forest's stream; the max over ranks is reported. The 1 GiB edge stream
+and 1 GiB pair stream are larger than L2 and each is read once per pass (the
+64 MiB forest stays resident, as it does between minibatches in use).
+
+``--impl reference`` times the CPU oracle (sequential union-find with path
+compression) on a bounded sample of each step's minibatch.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+METRIC = ("Bulk-Update edges/s & Bulk-Query queries/s (1 GB300), % HBM roofline; "
+          "p50/p99 batch latency")
+
+# Sector-model algorithmic bytes per unit (random 4-byte parent reads cost a
+# 32-byte sector): update 8 B edge + 2 x 32 B; query 8 B pair + 1 B answer +
+# 2 x 32 B; full compression 4 B read + 4 B write per vertex.
+BYTES_PER_UNIT = {"update": 72.0, "query": 73.0, "compress_all": 8.0,
+                  "compress_touched": 72.0, "labels": 12.0, "reset": 4.0}
+
+# Options of the launches this benchmark times, per workload (also used by
+# the full-size parity tests, so they check exactly this configuration).
+LAUNCH_OPTIONS = {
+    "rmat": {"block": 256, "edges_per_thread": 2, "compress_every": 1, "compress_scope": 0},
+    "uniform": {"block": 256, "edges_per_thread": 2, "compress_every": 1, "compress_scope": 0},
+    "grid": {"block": 256, "edges_per_thread": 2, "compress_every": 1, "compress_scope": 0},
+}
+
+
+def launch_options(workload: str) -> dict:
+    return dict(LAUNCH_OPTIONS[workload])
+
+
+def make_stream(workload: str, seed: int):
+    from paper_1602_05232_gb300 import inputs as I
+    if workload == "rmat":
+        return I.rmat_stream(seed=seed)
+    if workload == "uniform":
+        return I.uniform_stream(seed=seed)
+    if workload == "grid":
+        return I.grid_stream(seed=seed)
+    raise ValueError(workload)
+
+
+WORKLOAD_TEXT = {
+    "rmat": "R-MAT n=2^24 (a,b,c,d=.57,.19,.19,.05, permuted ids), 2^27 edges in 128 "
+            "Bulk-Updates of 2^20, each followed by a Bulk-Query of 2^20 uniform pairs",
+    "uniform": "uniform n=2^16, 2^20 edges in 16 Bulk-Updates of 2^16, each followed by "
+               "a Bulk-Query of 2^16 uniform pairs",
+    "grid": "shuffled 8192x8192 4-neighbour grid (n=2^26, 134,201,344 edges) in 32 "
+            "Bulk-Updates of 2^22, each followed by a Bulk-Query of 2^22 uniform pairs",
+}
+
+
+# ------------------------------------------------------------ distributed
+
+def dist_env() -> tuple[int, int, int]:
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def dist_init(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend)
+    return dist
+
+
+def dist_barrier(dist) -> None:
+    if dist is not None:
+        dist.barrier()
+
+
+def dist_max(dist, x: float, device=None) -> float:
+    """Max of a host float over ranks (the timing reduction; no data path)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_sum(dist, x: float, device=None) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- clocks
+
+CLOCK_FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+                "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+                "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    def __init__(self, device_index: int, period_ms: int = 50):
+        self.cmd = ["nvidia-smi", f"--id={device_index}", "--query-gpu=" + ",".join(CLOCK_FIELDS),
+                    "--format=csv,noheader,nounits", f"-lms={period_ms}"]
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < len(CLOCK_FIELDS):
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------- peaks
+
+def hbm_peak() -> tuple[float, str]:
+    p = ROOT / "MEASURED_PEAKS.json"
+    try:
+        return float(json.loads(p.read_text())["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    p = ROOT / "profiles" / "ncu_traffic.json"
+    try:
+        d = json.loads(p.read_text())
+        ent = d[workload][kernel]
+        from paper_1602_05232_gb300._build import cc_sources
+        import hashlib
+        h = hashlib.sha256(b"".join(s.read_bytes() for s in cc_sources())).hexdigest()[:16]
+        return ent["bytes_per_launch"] if ent.get("source_hash") == h else None
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------- GPU arm
+
+def run_gpu(args, rank: int, world: int, local_rank: int, dist) -> dict | None:
+    import torch
+    from paper_1602_05232_gb300 import cc
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    s = make_stream(args.workload, seed=rank)
+    B = s.batches
+    # whole stream in pinned host memory, then resident in HBM
+    h_edges = torch.empty((s.m, 2), dtype=torch.int32, pin_memory=True)
+    h_pairs = torch.empty((s.q, 2), dtype=torch.int32, pin_memory=True)
+    s.all_edges(out=h_edges.numpy())
+    s.all_queries(out=h_pairs.numpy())
+    eoff, qoff = s.edge_offsets(), s.query_offsets()
+    d_edges = h_edges.to(dev)
+    d_pairs = h_pairs.to(dev)
+    d_out = torch.empty(s.q, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    opts = launch_options(args.workload)
+
+    with torch.cuda.stream(stream):
+        f = cc.Forest(s.n, stream=stream, **opts)
+
+    def step(i: int, ev: list | None = None) -> None:
+        b = i % B
+        if b == 0 and i > 0:
+            f.reset()
+        e = d_edges[eoff[b]:eoff[b + 1]]
+        q = d_pairs[qoff[b]:qoff[b + 1]]
+        f.bulk_update(e)
+        f.bulk_query(q, out=d_out[qoff[b]:qoff[b + 1]])
+
+    # warm-up pass, then back to the empty graph
+    for i in range(args.warmup):
+        step(i)
+    f.reset()
+    stream.synchronize()
+    f.set_option("profile", 1)
+    f.kernel_stats(timing=True)           # clear timing sums
+    launches0 = f.kernel_stats()
+    edges_per_step = [int(eoff[(i % B) + 1] - eoff[i % B]) for i in range(args.steps)]
+    pairs_per_step = [int(qoff[(i % B) + 1] - qoff[i % B]) for i in range(args.steps)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+
+    dist_barrier(dist)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local_rank) as clk:
+        ev[0].record(stream)
+        for i in range(args.steps):
+            step(i)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+    dist_barrier(dist)
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    kstats = f.kernel_stats(timing=True)
+    launches1 = f.kernel_stats()
+    gpu_launches = sum(launches1[k] - launches0[k] for k in launches1)
+    f.set_option("profile", 0)
+    f.sync()
+
+    total_ms_max = dist_max(dist, total_ms, dev)
+    edges_all = dist_sum(dist, float(sum(edges_per_step)), dev)
+    pairs_all = dist_sum(dist, float(sum(pairs_per_step)), dev)
+    value = edges_all / (total_ms_max / 1e3)
+
+    # per-kernel breakdown and the roofline of the dominant kernel
+    peak, peak_kind = hbm_peak()
+    units = {"update": sum(edges_per_step), "query": sum(pairs_per_step),
+             "compress_all": s.n * (launches1["compress_all"] - launches0["compress_all"]),
+             "compress_touched": sum(edges_per_step),
+             "reset": s.n * (launches1["reset"] - launches0["reset"])}
+    kernels = {}
+    for k, (_, ms) in kstats.items():
+        cnt = launches1[k] - launches0[k]
+        if cnt and ms > 0:
+            gb = BYTES_PER_UNIT.get(k, 0.0) * units.get(k, 0) / 1e9
+            kernels[k] = {"launches": cnt, "ms_total": round(ms, 4), "us_avg": round(1e3 * ms / cnt, 3),
+                          "share": None, "GBps_algorithmic": round(gb / (ms / 1e3), 1) if gb else None}
+    tot_k = sum(v["ms_total"] for v in kernels.values()) or 1.0
+    for v in kernels.values():
+        v["share"] = round(v["ms_total"] / tot_k, 4)
+    dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
+    dk = kernels[dom]
+    per_launch_units = units[dom] / dk["launches"]
+    achieved = BYTES_PER_UNIT[dom] * per_launch_units / (dk["us_avg"] * 1e-6) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "peak_source": f"of {peak_kind}",
+                "bytes_per_unit": BYTES_PER_UNIT[dom],
+                "units_per_launch": per_launch_units,
+                "traffic": ncu_traffic(dom, args.workload)}
+
+    upd_ms = sum(kstats[k][1] for k in ("update", "compress_all", "compress_touched"))
+    qry_ms = kstats["query"][1]
+    e2e = run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist) if not args.no_e2e else None
+
+    f.close()
+    del d_edges, d_pairs
+    torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(s, h_edges.numpy(), h_pairs.numpy(), eoff, qoff, args.cpu_seconds)
+
+    lat = sorted(step_ms)
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "edges/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms_max / args.steps, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded R-MAT / uniform / grid generators; no dataset)",
+        "config": {"workload": WORKLOAD_TEXT[args.workload], "n": s.n, "edges_per_pass": s.m,
+                   "batch": int(eoff[1]), "query_batch": int(qoff[1]),
+                   "form": "plain (one launch per bulk operation)", "options": opts,
+                   "l2": "inputs larger than L2: 1 GiB edge + 1 GiB pair streams, each read "
+                         "once per pass; the forest (4n bytes) persists across steps",
+                   "parallelism": f"replicas x{world} (independent streams, no collective)"},
+        "queries_per_s": round(pairs_all / (total_ms_max / 1e3), 1),
+        "update_edges_per_s_kernels": round(sum(edges_per_step) / (upd_ms / 1e3), 1) if upd_ms else None,
+        "query_per_s_kernel": round(sum(pairs_per_step) / (qry_ms / 1e3), 1) if qry_ms else None,
+        "latency_ms": {"p50": round(lat[len(lat) // 2], 4),
+                       "p99": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 4),
+                       "what": "device time of one step (update + compress + query)"},
+        "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
+        "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu,
+    }
+    return out
+
+
+def run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist) -> dict:
+    """Same metric through the public API from HOST buffers: every step copies
+    its minibatch and query pairs from pinned host memory to the device and
+    reads its answers back into pinned host memory, inside the timed region."""
+    import torch
+    from paper_1602_05232_gb300 import cc
+
+    B = s.batches
+    kmax = int(np.max(np.diff(eoff)))
+    qmax = int(np.max(np.diff(qoff)))
+    stream = torch.cuda.Stream(device=dev)
+    d_e = torch.empty((kmax, 2), dtype=torch.int32, device=dev)
+    d_q = torch.empty((qmax, 2), dtype=torch.int32, device=dev)
+    d_o = torch.empty(qmax, dtype=torch.uint8, device=dev)
+    h_o = torch.empty(s.q, dtype=torch.uint8, pin_memory=True)
+    steps = min(args.steps, B)
+    with torch.cuda.stream(stream):
+        f = cc.Forest(s.n, stream=stream, **launch_options(args.workload))
+
+        def step(i):
+            b = i % B
+            k, q = int(eoff[b + 1] - eoff[b]), int(qoff[b + 1] - qoff[b])
+            d_e[:k].copy_(h_edges[eoff[b]:eoff[b + 1]], non_blocking=True)
+            d_q[:q].copy_(h_pairs[qoff[b]:qoff[b + 1]], non_blocking=True)
+            f.bulk_update(d_e[:k])
+            f.bulk_query(d_q[:q], out=d_o[:q])
+            h_o[qoff[b]:qoff[b + 1]].copy_(d_o[:q], non_blocking=True)
+            return k, q
+
+        for i in range(min(args.warmup, B)):
+            step(i)
+        f.reset()
+        stream.synchronize()
+        dist_barrier(dist)
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h2d = d2h = edges = 0
+        for i in range(steps):
+            k, q = step(i)
+            edges += k
+            h2d += 8 * k + 8 * q
+            d2h += q
+        b_.record(stream)
+        stream.synchronize()
+        dist_barrier(dist)
+        f.sync()
+        f.close()
+    ms = dist_max(dist, a.elapsed_time(b_), dev)
+    edges_all = dist_sum(dist, float(edges), dev)
+    return {"value": round(edges_all / (ms / 1e3), 1), "unit": "edges/s",
+            "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
+            "steps": steps, "what": "pinned host -> device copies, update, query, answers "
+                                    "-> pinned host, all on one stream"}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def cpu_baseline(s, edges: np.ndarray, pairs: np.ndarray, eoff, qoff, seconds: float) -> dict:
+    """The oracle (single-threaded sequential union-find) on the host: the
+    stream's minibatches in order from the empty graph until `seconds` of
+    oracle time have been spent."""
+    import oracle
+    uf = oracle.OracleUF(s.n)
+    t_total, e_done, q_done, b = 0.0, 0, 0, 0
+    while b < s.batches and t_total < seconds:
+        e = edges[eoff[b]:eoff[b + 1]]
+        q = pairs[qoff[b]:qoff[b + 1]]
+        t0 = time.perf_counter()
+        uf.bulk_update(e)
+        uf.bulk_query(q)
+        t_total += time.perf_counter() - t0
+        e_done += len(e)
+        q_done += len(q)
+        b += 1
+    return {"value": round(e_done / t_total, 1), "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {b} of {s.batches} minibatches ({e_done} edges + {q_done} query "
+                      f"pairs) from the empty graph, {t_total:.1f} s on one host core",
+            "host_cores_available": os.cpu_count()}
+
+
+def run_reference(args, rank: int, world: int) -> dict | None:
+    """--impl reference: the CPU oracle on a bounded sample of every step."""
+    if rank != 0:
+        return None
+    import oracle
+    s = make_stream(args.workload, seed=0)
+    B = s.batches
+    frac = args.ref_fraction
+    eoff, qoff = s.edge_offsets(), s.query_offsets()
+    uf = oracle.OracleUF(s.n)
+    cache = {}
+
+    def batch(b):
+        if b not in cache:
+            ke = max(1, int(eoff[b + 1] - eoff[b]) // frac)
+            kq = max(1, int(qoff[b + 1] - qoff[b]) // frac)
+            cache[b] = (s.edges_range(int(eoff[b]), int(eoff[b]) + ke),
+                        uniform_slice(s, b, kq))
+        return cache[b]
+
+    def step(i):
+        nonlocal uf
+        b = i % B
+        if b == 0 and i > 0:
+            uf = oracle.OracleUF(s.n)
+        e, q = batch(b)
+        uf.bulk_update(e)
+        uf.bulk_query(q)
+        return len(e), len(q)
+
+    for i in range(min(B, args.steps)):
+        batch(i % B)
+    for i in range(args.warmup):
+        step(i)
+    uf = oracle.OracleUF(s.n)
+    t0 = time.perf_counter()
+    edges = 0
+    for i in range(args.steps):
+        k, _ = step(i)
+        edges += k
+    dt = time.perf_counter() - t0
+    v = edges / dt
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "edges/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * dt / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload],
+                       "sample": f"each step applies the first 1/{frac} of its minibatch's edges "
+                                 f"and queries the first 1/{frac} of its pairs"},
+            "cpu_baseline": {"value": round(v, 1), "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": f"1/{frac} of every minibatch, {args.steps} steps"},
+            "e2e": {"value": round(v, 1), "unit": "edges/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def uniform_slice(s, b: int, kq: int) -> np.ndarray:
+    from paper_1602_05232_gb300 import inputs as I
+    return I.uniform_pairs(s.n, kq, s.seed, I.TAG_QUERIES, int(s.query_offsets()[b]))
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5120)
+    ap.add_argument("--warmup", type=int, default=16)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", choices=sorted(LAUNCH_OPTIONS), default="rmat")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-fraction", type=int, default=64)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        dist = dist_init(world, "nccl")
+        out = run_gpu(args, rank, world, local_rank, dist)
+        if dist is not None:
+            dist.destroy_process_group()
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

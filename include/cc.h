@@ -1,0 +1,190 @@
+/*
+ * libcc -- bulk-parallel incremental graph connectivity on one GB300 (sm_103a).
+ *
+ * The data structure of Section 3 ("Simple Bulk-Parallel Data Structure"):
+ * a union-find forest over the vertex set {0, ..., n-1}, kept in device
+ * memory as one int32 parent array (parent[v] == v for a root). Two bulk
+ * operations act on it (Section 1, "Model"):
+ *
+ *   Bulk-Update  folds a minibatch of edges into the forest (Algorithm 2);
+ *   Bulk-Query   answers, for each vertex pair of a minibatch, whether the two
+ *                are connected by the edges added so far (Algorithm 1).
+ *
+ * Link rule. Hooking always makes the root with the larger id a child of the
+ * root with the smaller id, so parent[v] <= v holds for every v at all times
+ * and the root of each tree is the smallest id in its component. Section 3
+ * links by size; any rule that joins two distinct roots is correct for
+ * connectivity (the correctness lemma of Section 3.2 needs only that), and
+ * this one needs no sizes array and no locks.
+ *
+ * Conventions for every entry point:
+ *  - Vertex ids are int32 in [0, n). An edge or a query pair is two int32s,
+ *    stored flat as u0, v0, u1, v1, ... (8 bytes per pair). A pointer of 16-
+ *    byte alignment gets 16-byte vector loads; 4-byte alignment is the minimum.
+ *  - Array arguments are DEVICE pointers owned by the caller unless stated
+ *    otherwise. They must stay valid until the handle's stream has executed
+ *    the call (calls are asynchronous).
+ *  - All work is enqueued in order on the handle's stream, so each bulk
+ *    operation completes before the next one starts (the paper's ordering
+ *    rule, Section 1). A handle must not be used from two host threads at once.
+ *  - Argument errors are found on the host and returned at once, with no
+ *    state change. Errors found by kernels (out-of-range ids, a broken forest)
+ *    set a device status word; they are returned by the next cc_sync() (or
+ *    any call that synchronises), which also clears the word.
+ *  - No entry point aborts the process. cc_last_error_string() gives the text
+ *    of the last failure on the calling thread.
+ */
+#ifndef LIBCC_CC_H
+#define LIBCC_CC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cc_ctx cc_ctx;
+/* Same object as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* cc_stream_t;
+
+typedef enum {
+    CC_OK = 0,
+    CC_ERR_ARG = 1,      /* bad argument (null handle/pointer, bad size, misalignment) */
+    CC_ERR_OOM = 2,      /* a device allocation failed */
+    CC_ERR_CUDA = 3,     /* a CUDA runtime call or a launch failed */
+    CC_ERR_RANGE = 4,    /* a kernel met a vertex id outside [0, n); see below */
+    CC_ERR_CORRUPT = 5,  /* a kernel met parent[v] > v (only after a bad load) */
+    CC_ERR_LABELS = 6,   /* cc_load_labels: the array is not a valid labelling */
+    CC_ERR_UNSUPPORTED = 7
+} cc_status;
+
+/* Compression scopes for cc_compress and the automatic policy. */
+typedef enum {
+    CC_COMPRESS_ALL = 0,      /* every vertex points at its root afterwards */
+    CC_COMPRESS_TOUCHED = 1   /* only the endpoints of a given edge array, and their paths */
+} cc_compress_scope;
+
+/* Tunables (cc_set_option / cc_get_option). */
+typedef enum {
+    CC_OPT_BLOCK = 0,            /* threads per block for the bulk kernels: 64..1024, multiple of 32 (default 256) */
+    CC_OPT_EDGES_PER_THREAD = 1, /* edges (or pairs) per thread in update and query: 1, 2 or 4 (default 2) */
+    CC_OPT_COMPRESS_EVERY = 2,   /* cc_bulk_update compresses after every c-th call; 0 = never (default 1) */
+    CC_OPT_COMPRESS_SCOPE = 3,   /* scope of that automatic compression: a cc_compress_scope (default ALL) */
+    CC_OPT_QUERY_HALVING = 4,    /* 1: Bulk-Query finds also halve paths (they write); 0: read-only finds (default) */
+    CC_OPT_PROFILE = 5,          /* 1: time every kernel with CUDA events on the handle's stream */
+    CC_OPT__COUNT = 6
+} cc_option;
+
+/* Kernel kinds reported by the launch counters and the profiler. */
+typedef enum {
+    CC_K_UPDATE = 0,
+    CC_K_COMPRESS_ALL = 1,
+    CC_K_COMPRESS_TOUCHED = 2,
+    CC_K_QUERY = 3,
+    CC_K_LABELS = 4,
+    CC_K_RESET = 5,
+    CC_K_LOAD = 6,
+    CC_K_SEGMENTED = 7,
+    CC_K__COUNT = 8
+} cc_kernel_kind;
+
+/* ------------------------------------------------------------ lifetime */
+
+/* Create a forest over n vertices, 1 <= n <= 2^31 - 1, on the current CUDA
+ * device, starting as n singletons (the empty graph G_0 of Section 1). The
+ * library allocates parent[n] (4n bytes) and a status word; both are freed by
+ * cc_destroy. *out receives the handle (NULL on failure). Enqueues one kernel
+ * on the legacy default stream and waits for it.
+ * Errors: CC_ERR_ARG (n out of range, out NULL), CC_ERR_OOM, CC_ERR_CUDA. */
+cc_status cc_create(int64_t n, cc_ctx** out);
+
+/* Wait for the handle's stream and free everything. NULL is a no-op. */
+cc_status cc_destroy(cc_ctx* ctx);
+
+/* Bind the handle to a stream (a cudaStream_t of the handle's device). Work
+ * already enqueued stays on the old stream; the caller orders the two. */
+cc_status cc_set_stream(cc_ctx* ctx, cc_stream_t stream);
+
+/* Wait for all work enqueued on the handle, then return and clear any error a
+ * kernel recorded since the last sync: CC_ERR_RANGE if an edge or a query had
+ * an endpoint outside [0, n) (that edge was skipped and that query answered 0;
+ * the rest of the minibatch was applied), else CC_ERR_CORRUPT if a kernel met
+ * a parent pointer to a larger id. */
+cc_status cc_sync(cc_ctx* ctx);
+
+/* Back to n singletons (G_0), asynchronously. Clears the union counter. */
+cc_status cc_reset(cc_ctx* ctx);
+
+/* ------------------------------------------------------- bulk operations */
+
+/* Bulk-Update (Algorithm 2; Section 3.2): add the k edges at `edges`
+ * (device, 2k int32, u0 v0 u1 v1 ...) to the graph. One fused kernel: per
+ * edge, find both roots with path halving (Algorithm 2's relabel step, with
+ * the walk shortening of Section 5.1), drop it if the roots agree (the self-
+ * loop filter of Algorithm 2), else hook the larger root under the smaller
+ * with a compare-and-swap, re-finding and retrying when another edge moved
+ * that root first. This replaces Algorithm 2's connected-components step and
+ * Parallel-Join (Algorithm 3): both only exist to join distinct roots without
+ * conflicts. The order of edges inside a minibatch does not matter (Section
+ * 2); self-loops and repeated edges are legal no-ops. k = 0 is a no-op. Then,
+ * per CC_OPT_COMPRESS_EVERY / _SCOPE, one compression pass (cc_compress).
+ * Errors: CC_ERR_ARG (k < 0, k > 2^31 - 1, edges NULL with k > 0); ids outside
+ * [0, n) are reported by cc_sync as CC_ERR_RANGE. */
+cc_status cc_bulk_update(cc_ctx* ctx, const int32_t* edges, int64_t k);
+
+/* Bulk-Query (Algorithm 1; Section 3.1): out[i] = 1 if pairs[2i] and
+ * pairs[2i+1] are connected by the edges added so far, else 0. `pairs`:
+ * device, 2k int32; `out`: device, k bytes, written by the kernel. A pair
+ * (u, u) answers 1. Finds are read-only unless CC_OPT_QUERY_HALVING is 1;
+ * when the forest is known to be flat (right after a full compression, with
+ * no update since) each answer is the equality of the two parents.
+ * Errors: CC_ERR_ARG; ids outside [0, n) answer 0 and are reported by cc_sync. */
+cc_status cc_bulk_query(cc_ctx* ctx, const int32_t* pairs, int64_t k, uint8_t* out);
+
+/* Path compression as a separate pass (Section 5.1, "Path Compression":
+ * after the root is found, the path is walked again and every node on it is
+ * pointed at the root). CC_COMPRESS_ALL does this for every vertex, leaving
+ * every tree of height at most one; CC_COMPRESS_TOUCHED does it for the 2k
+ * endpoints of `edges` (device, 2k int32). Answers never depend on it. */
+cc_status cc_compress(cc_ctx* ctx, int32_t scope, const int32_t* edges, int64_t k);
+
+/* Component labels: out[v] = the smallest vertex id connected to v (device,
+ * n int32). Under the link rule above this is v's root; computing it also
+ * compresses the forest fully. */
+cc_status cc_labels(cc_ctx* ctx, int32_t* out);
+
+/* Replace the forest by a labelling (the inverse of cc_labels, for
+ * checkpoint and resume; the whole state of the structure is the O(n) parent
+ * array, Theorem 2). `labels` (device, n int32) must satisfy 0 <= labels[v]
+ * <= v and labels[labels[v]] == labels[v]; any labelling of a graph by
+ * minimum component ids does. Synchronises. On CC_ERR_LABELS the forest is
+ * unchanged. */
+cc_status cc_load_labels(cc_ctx* ctx, const int32_t* labels);
+
+/* Copy the raw parent array (device, n int32) -- for invariant checks. */
+cc_status cc_copy_parent(cc_ctx* ctx, int32_t* out);
+
+/* Number of connected components (n minus the successful hooks since create
+ * or reset). Synchronises; *out is a host int64. */
+cc_status cc_components(cc_ctx* ctx, int64_t* out);
+
+/* ----------------------------------------------------------- tunables */
+
+cc_status cc_set_option(cc_ctx* ctx, int32_t option, int64_t value);
+cc_status cc_get_option(const cc_ctx* ctx, int32_t option, int64_t* value);
+
+/* Kernel launches made by the handle so far, per cc_kernel_kind (host array
+ * of CC_K__COUNT uint64), and, when CC_OPT_PROFILE is on, the summed CUDA-
+ * event duration of those launches in milliseconds (host array of CC_K__COUNT
+ * doubles; NULL to skip). Synchronises when ms is not NULL; reading resets the
+ * timing sums, not the counters. */
+cc_status cc_kernel_stats(cc_ctx* ctx, uint64_t* launches, double* ms);
+
+int64_t cc_num_vertices(const cc_ctx* ctx);
+const char* cc_status_string(cc_status s);
+const char* cc_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBCC_CC_H */

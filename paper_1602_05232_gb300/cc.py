@@ -1,0 +1,217 @@
+"""Python binding of libcc (the C-ABI in include/cc.h).
+
+Argument marshalling only: tensors are checked (CUDA, int32/uint8,
+contiguous) and their device pointers, sizes and the current CUDA stream are
+passed through ctypes. Every step of the bulk operations runs in libcc's
+kernels. There is no fallback: if ``libcc.so`` is missing or cannot be
+loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import torch
+
+from ._build import LIBCC
+
+CC_OK, CC_ERR_ARG, CC_ERR_OOM, CC_ERR_CUDA, CC_ERR_RANGE, CC_ERR_CORRUPT, CC_ERR_LABELS, \
+    CC_ERR_UNSUPPORTED = range(8)
+COMPRESS_ALL, COMPRESS_TOUCHED = 0, 1
+OPT_BLOCK, OPT_EDGES_PER_THREAD, OPT_COMPRESS_EVERY, OPT_COMPRESS_SCOPE, OPT_QUERY_HALVING, \
+    OPT_PROFILE = range(6)
+OPTIONS = {"block": OPT_BLOCK, "edges_per_thread": OPT_EDGES_PER_THREAD,
+           "compress_every": OPT_COMPRESS_EVERY, "compress_scope": OPT_COMPRESS_SCOPE,
+           "query_halving": OPT_QUERY_HALVING, "profile": OPT_PROFILE}
+KERNELS = ["update", "compress_all", "compress_touched", "query", "labels", "reset", "load",
+           "segmented"]
+
+_lib: ctypes.CDLL | None = None
+
+
+class CCError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_status_name(status)}: {message}")
+        self.status = status
+
+
+def _status_name(s: int) -> str:
+    names = ["CC_OK", "CC_ERR_ARG", "CC_ERR_OOM", "CC_ERR_CUDA", "CC_ERR_RANGE",
+             "CC_ERR_CORRUPT", "CC_ERR_LABELS", "CC_ERR_UNSUPPORTED"]
+    return names[s] if 0 <= s < len(names) else f"status {s}"
+
+
+def load(path: str | Path | None = None) -> ctypes.CDLL:
+    """Load libcc.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = Path(path) if path else LIBCC
+    if not p.exists():
+        raise RuntimeError(f"libcc.so not found at {p}: build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(str(p))
+    vp, i64, i32, u64p = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
+    sig = {
+        "cc_create": [i64, ctypes.POINTER(ctypes.c_void_p)],
+        "cc_destroy": [vp],
+        "cc_set_stream": [vp, vp],
+        "cc_sync": [vp],
+        "cc_reset": [vp],
+        "cc_bulk_update": [vp, vp, i64],
+        "cc_bulk_query": [vp, vp, i64, vp],
+        "cc_compress": [vp, i32, vp, i64],
+        "cc_labels": [vp, vp],
+        "cc_load_labels": [vp, vp],
+        "cc_copy_parent": [vp, vp],
+        "cc_components": [vp, ctypes.POINTER(ctypes.c_int64)],
+        "cc_set_option": [vp, i32, i64],
+        "cc_get_option": [vp, i32, ctypes.POINTER(ctypes.c_int64)],
+        "cc_kernel_stats": [vp, u64p, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.cc_num_vertices.argtypes = [vp]
+    L.cc_num_vertices.restype = i64
+    L.cc_status_string.argtypes = [ctypes.c_int]
+    L.cc_status_string.restype = ctypes.c_char_p
+    L.cc_last_error_string.argtypes = []
+    L.cc_last_error_string.restype = ctypes.c_char_p
+    if path is None:
+        _lib = L
+    return L
+
+
+def check(status: int, L: ctypes.CDLL | None = None) -> None:
+    if status != CC_OK:
+        L = L or load()
+        raise CCError(status, (L.cc_last_error_string() or b"").decode())
+
+
+def _pairs_ptr(t: torch.Tensor, name: str) -> tuple[int, int]:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name}: expected a CUDA tensor")
+    if t.dtype != torch.int32 or not t.is_contiguous():
+        raise TypeError(f"{name}: expected a contiguous int32 tensor")
+    if t.numel() % 2:
+        raise ValueError(f"{name}: expected (k, 2) pairs")
+    return t.data_ptr(), t.numel() // 2
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if isinstance(stream, torch.cuda.Stream) else int(stream)
+
+
+class Forest:
+    """A device-resident union-find forest over vertices 0..n-1 (libcc handle).
+
+    All calls are enqueued on the bound stream (default: the current torch
+    stream at construction)."""
+
+    def __init__(self, n: int, stream=None, **options):
+        self._L = load()
+        h = ctypes.c_void_p()
+        check(self._L.cc_create(int(n), ctypes.byref(h)), self._L)
+        self._h = h
+        self.n = int(n)
+        self.set_stream(stream)
+        for k, v in options.items():
+            self.set_option(k, v)
+
+    # lifetime ---------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            check(self._L.cc_destroy(self._h), self._L)
+            self._h = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None):
+                self._L.cc_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream=None) -> None:
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        check(self._L.cc_set_stream(self._h, _stream_handle(self.stream)), self._L)
+
+    def sync(self) -> None:
+        check(self._L.cc_sync(self._h), self._L)
+
+    def reset(self) -> None:
+        check(self._L.cc_reset(self._h), self._L)
+
+    # bulk operations ---------------------------------------------------
+    def bulk_update(self, edges: torch.Tensor) -> None:
+        p, k = _pairs_ptr(edges, "edges")
+        check(self._L.cc_bulk_update(self._h, p, k), self._L)
+
+    def bulk_query(self, pairs: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        p, k = _pairs_ptr(pairs, "pairs")
+        if out is None:
+            out = torch.empty(k, dtype=torch.uint8, device=pairs.device)
+        if out.dtype != torch.uint8 or not out.is_contiguous() or out.numel() < k or not out.is_cuda:
+            raise TypeError("out: expected a contiguous CUDA uint8 tensor of k elements")
+        check(self._L.cc_bulk_query(self._h, p, k, out.data_ptr()), self._L)
+        return out
+
+    def compress(self, scope: str = "all", edges: torch.Tensor | None = None) -> None:
+        if scope == "all":
+            check(self._L.cc_compress(self._h, COMPRESS_ALL, None, 0), self._L)
+        else:
+            p, k = _pairs_ptr(edges, "edges")
+            check(self._L.cc_compress(self._h, COMPRESS_TOUCHED, p, k), self._L)
+
+    def labels(self, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        if out.dtype != torch.int32 or not out.is_contiguous() or out.numel() < self.n:
+            raise TypeError("out: expected a contiguous int32 tensor of n elements")
+        check(self._L.cc_labels(self._h, out.data_ptr()), self._L)
+        return out
+
+    def load_labels(self, labels: torch.Tensor) -> None:
+        if labels.dtype != torch.int32 or not labels.is_contiguous() or labels.numel() != self.n:
+            raise TypeError("labels: expected a contiguous int32 tensor of n elements")
+        check(self._L.cc_load_labels(self._h, labels.data_ptr()), self._L)
+
+    def parent(self) -> torch.Tensor:
+        out = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        check(self._L.cc_copy_parent(self._h, out.data_ptr()), self._L)
+        return out
+
+    def components(self) -> int:
+        v = ctypes.c_int64()
+        check(self._L.cc_components(self._h, ctypes.byref(v)), self._L)
+        return v.value
+
+    # tunables and counters ---------------------------------------------
+    def set_option(self, name: str, value: int) -> None:
+        check(self._L.cc_set_option(self._h, OPTIONS[name], int(value)), self._L)
+
+    def get_option(self, name: str) -> int:
+        v = ctypes.c_int64()
+        check(self._L.cc_get_option(self._h, OPTIONS[name], ctypes.byref(v)), self._L)
+        return v.value
+
+    def kernel_stats(self, timing: bool = False) -> dict:
+        """{kind: launches} and, with timing=True, {kind: (launches, ms)}
+        (the ms sums cover launches since the previous timing read)."""
+        n = len(KERNELS)
+        counts = (ctypes.c_uint64 * n)()
+        ms = (ctypes.c_double * n)() if timing else None
+        check(self._L.cc_kernel_stats(self._h, counts, ms), self._L)
+        if timing:
+            return {k: (int(counts[i]), float(ms[i])) for i, k in enumerate(KERNELS)}
+        return {k: int(counts[i]) for i, k in enumerate(KERNELS)}

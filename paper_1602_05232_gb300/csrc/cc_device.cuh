@@ -1,0 +1,115 @@
+// Device primitives of the union-find forest: find and hook.
+//
+// Forest invariant: parent[x] <= x for every x, with equality exactly at the
+// roots. Hooks link the larger root under the smaller, and path halving and
+// compression only repoint a node at one of its ancestors, so every write
+// keeps the invariant. Consequences used throughout:
+//  * every walk strictly decreases the id, so it ends within n steps (no
+//    iteration limit is needed, and none can livelock);
+//  * once a node stops being a root it never becomes one again, so only roots
+//    are ever compare-and-swapped and only non-roots ever get plain stores;
+//  * a value read late or early is still an ancestor: two endpoints that reach
+//    the same node are connected, whatever else is happening.
+#pragma once
+
+#include <cstdint>
+
+#include "cc_internal.cuh"
+
+namespace cc {
+
+__device__ __forceinline__ void flag(DevState* ds, unsigned bit) { atomicOr(&ds->status, bit); }
+
+__device__ __forceinline__ bool in_range(int x, int n) { return (unsigned)x < (unsigned)n; }
+
+// Root of x's tree, given p = parent[x] already read and p != x. Walks with
+// path halving: each visited node is repointed at its grandparent, which
+// roughly halves the path for later walks (the Section 5.1 idea of making
+// later finds cheaper, done on the way up rather than in a second pass).
+__device__ __forceinline__ int find_from(int* parent, int x, int p, DevState* ds) {
+    while (true) {
+        if (p > x) {  // broken invariant: stop rather than loop
+            flag(ds, ST_CORRUPT);
+            return x;
+        }
+        int gp = parent[p];
+        if (gp == p) return p;
+        parent[x] = gp;
+        x = gp;
+        p = parent[x];
+        if (p == x) return x;
+    }
+}
+
+__device__ __forceinline__ int find_halving(int* parent, int x, DevState* ds) {
+    int p = parent[x];
+    return p == x ? x : find_from(parent, x, p, ds);
+}
+
+// Join the trees of roots-or-former-roots ru and rv: the larger root becomes a
+// child of the smaller one with a compare-and-swap that succeeds only while it
+// is still a root. If another thread linked it first, continue from its new
+// root. Each failed round strictly lowers max(ru, rv), so it ends. Returns 1
+// if this call made the link, 0 if the two were already joined.
+__device__ __forceinline__ int hook(int* parent, int ru, int rv, DevState* ds) {
+    while (ru != rv) {
+        int hi = ru > rv ? ru : rv;
+        int lo = ru > rv ? rv : ru;
+        int old = atomicCAS(parent + hi, hi, lo);
+        if (old == hi) return 1;
+        if (old > hi) {
+            flag(ds, ST_CORRUPT);
+            return 0;
+        }
+        int r = find_halving(parent, old, ds);
+        if (hi == ru) ru = r; else rv = r;
+    }
+    return 0;
+}
+
+// Read-only walk to the root from x with p = parent[x] already read.
+__device__ __forceinline__ int walk_root(const int* parent, int x, int p) {
+    while (p < x) {
+        x = p;
+        p = parent[x];
+    }
+    return x;
+}
+
+// Load E pairs starting at pair index e0 of a flat u0 v0 u1 v1 ... array.
+// vec: 2 = the array is 16-byte aligned, 1 = 8-byte, 0 = 4-byte. Pairs past k
+// are left as (0, 0) and must be ignored by the caller. Streaming loads: each
+// pair is read once, so it should not displace the forest from L2.
+template <int E>
+__device__ __forceinline__ void load_pairs(const int* __restrict__ a, int64_t e0, int64_t k,
+                                           int vec, int (&u)[E], int (&v)[E]) {
+    if (e0 + E <= k) {
+        if (E % 2 == 0 && vec == 2) {
+#pragma unroll
+            for (int i = 0; i < E / 2; i++) {
+                int4 q = __ldcs(reinterpret_cast<const int4*>(a + 2 * e0) + i);
+                u[2 * i] = q.x; v[2 * i] = q.y; u[2 * i + 1] = q.z; v[2 * i + 1] = q.w;
+            }
+            return;
+        }
+        if (vec >= 1) {
+#pragma unroll
+            for (int i = 0; i < E; i++) {
+                int2 q = __ldcs(reinterpret_cast<const int2*>(a + 2 * e0) + i);
+                u[i] = q.x; v[i] = q.y;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        if (e0 + i < k) {
+            u[i] = __ldcs(a + 2 * (e0 + i));
+            v[i] = __ldcs(a + 2 * (e0 + i) + 1);
+        } else {
+            u[i] = 0; v[i] = 0;
+        }
+    }
+}
+
+}  // namespace cc

@@ -1,0 +1,54 @@
+// Internal declarations shared by the libcc translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "cc.h"
+
+namespace cc {
+
+// Bits of the device status word.
+enum : unsigned {
+    ST_RANGE = 1u,    // an edge or query endpoint was outside [0, n)
+    ST_CORRUPT = 2u,  // parent[x] > x was seen (cannot happen through the API)
+};
+
+// Device-side bookkeeping of one handle (one small allocation).
+struct DevState {
+    unsigned status;            // ST_* bits, cleared by cc_sync
+    unsigned labels_bad;        // set by the label validator
+    unsigned long long unions;  // successful hooks since create / reset
+    unsigned long long roots;   // roots counted by the label validator
+};
+
+struct Launch {
+    int block;  // threads per block, multiple of 32
+    int ept;    // edges (pairs) per thread: 1, 2 or 4
+};
+
+// Alignment class of a pair array: 2 = 16-byte, 1 = 8-byte, 0 = 4-byte.
+int pair_vec(const void* p);
+
+cudaError_t launch_reset(int* parent, int64_t n, int block, cudaStream_t s);
+
+cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevState* ds,
+                          Launch cfg, cudaStream_t s);
+
+// mode: 0 read-only finds, 1 finds with path halving, 2 flat forest (parent
+// equality decides).
+cudaError_t launch_query(int* parent, int n, const int* pairs, int64_t k, uint8_t* out,
+                         DevState* ds, int mode, Launch cfg, cudaStream_t s);
+
+// Full compression; also writes labels to `out` when it is not null.
+cudaError_t launch_compress_all(int* parent, int64_t n, int* out, DevState* ds, int block,
+                                cudaStream_t s);
+
+cudaError_t launch_compress_touched(int* parent, int n, const int* edges, int64_t k,
+                                    DevState* ds, Launch cfg, cudaStream_t s);
+
+// Checks 0 <= lab[v] <= v and lab[lab[v]] == lab[v]; counts roots.
+cudaError_t launch_validate_labels(const int* lab, int64_t n, DevState* ds, int block,
+                                   cudaStream_t s);
+
+}  // namespace cc

@@ -1,0 +1,355 @@
+// Kernels of the plain (one launch per bulk operation) path and their launchers.
+#include <cstdint>
+
+#include "cc_device.cuh"
+#include "cc_internal.cuh"
+
+namespace cc {
+
+int pair_vec(const void* p) {
+    uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    return (a % 16 == 0) ? 2 : (a % 8 == 0) ? 1 : 0;
+}
+
+static inline unsigned blocks_for(int64_t work, int64_t per_block) {
+    return (unsigned)((work + per_block - 1) / per_block);
+}
+
+// ------------------------------------------------------------------ reset
+
+// parent[v] = v: n singletons, the empty graph G_0.
+__global__ void k_reset(int* __restrict__ parent, int64_t n) {
+    int64_t v0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (v0 + 4 <= n) {
+        int x = (int)v0;
+        reinterpret_cast<int4*>(parent)[v0 / 4] = make_int4(x, x + 1, x + 2, x + 3);
+    } else {
+        for (int64_t v = v0; v < n; v++) parent[v] = (int)v;
+    }
+}
+
+cudaError_t launch_reset(int* parent, int64_t n, int block, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_reset<<<blocks_for(n, 4LL * block), block, 0, s>>>(parent, n);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ Bulk-Update
+
+// One fused pass of Algorithm 2 over E edges per thread. The first parent
+// reads of both endpoints of all E edges are issued together; equal parents
+// mean the edge joins a tree to itself and is dropped at once (the common
+// case once trees are flat). Otherwise both roots are found with path
+// halving and hooked.
+template <int E>
+__global__ void __launch_bounds__(1024)
+k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
+         DevState* __restrict__ ds) {
+    const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
+    int made = 0;
+    if (e0 < k) {
+        int u[E], v[E], pu[E], pv[E];
+        bool ok[E];
+        bool bad = false;
+        load_pairs<E>(edges, e0, k, vec, u, v);
+#pragma unroll
+        for (int i = 0; i < E; i++) {
+            ok[i] = e0 + i < k;
+            if (ok[i] && !(in_range(u[i], n) && in_range(v[i], n))) {
+                ok[i] = false;
+                bad = true;
+            }
+            pu[i] = 0;
+            pv[i] = 0;
+        }
+#pragma unroll
+        for (int i = 0; i < E; i++) {
+            if (ok[i]) {
+                pu[i] = parent[u[i]];
+                pv[i] = parent[v[i]];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < E; i++) {
+            if (!ok[i] || pu[i] == pv[i]) continue;
+            int ru = pu[i] == u[i] ? u[i] : find_from(parent, u[i], pu[i], ds);
+            int rv = pv[i] == v[i] ? v[i] : find_from(parent, v[i], pv[i], ds);
+            made += hook(parent, ru, rv, ds);
+        }
+        if (bad) flag(ds, ST_RANGE);
+    }
+    made = __reduce_add_sync(0xffffffffu, made);
+    if ((threadIdx.x & 31) == 0 && made) atomicAdd(&ds->unions, (unsigned long long)made);
+}
+
+cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevState* ds,
+                          Launch cfg, cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    const int vec = pair_vec(edges);
+    const unsigned g = blocks_for(k, (int64_t)cfg.ept * cfg.block);
+    switch (cfg.ept) {
+        case 1: k_update<1><<<g, cfg.block, 0, s>>>(parent, n, edges, k, vec, ds); break;
+        case 2: k_update<2><<<g, cfg.block, 0, s>>>(parent, n, edges, k, vec, ds); break;
+        default: k_update<4><<<g, cfg.block, 0, s>>>(parent, n, edges, k, vec, ds); break;
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- Bulk-Query
+
+template <int E>
+__device__ __forceinline__ void store_answers(uint8_t* __restrict__ out, int64_t e0, int64_t k,
+                                              bool ovec, const uint8_t (&a)[E]) {
+    if (ovec && e0 + E <= k) {
+        if (E == 4) {
+            uchar4 w = make_uchar4(a[0], a[E > 1 ? 1 : 0], a[E > 2 ? 2 : 0], a[E > 3 ? 3 : 0]);
+            __stcs(reinterpret_cast<uchar4*>(out + e0), w);
+            return;
+        }
+        if (E == 2) {
+            uchar2 w = make_uchar2(a[0], a[E > 1 ? 1 : 0]);
+            __stcs(reinterpret_cast<uchar2*>(out + e0), w);
+            return;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < E; i++)
+        if (e0 + i < k) out[e0 + i] = a[i];
+}
+
+// Algorithm 1 over E pairs per thread. Lanes of a warp own consecutive pairs,
+// so the pair loads (16 B per lane) and the answer stores (E bytes per lane)
+// are coalesced across the warp.
+//  MODE 0: read-only finds through the read-only data path; the 2E walks of a
+//          thread advance in lockstep so their loads overlap.
+//  MODE 1: finds with path halving (they write, so ordinary loads).
+//  MODE 2: flat forest (every tree of height <= 1): parent equality decides.
+template <int E, int MODE>
+__global__ void __launch_bounds__(1024)
+k_query(int* __restrict__ parent, int n, const int* __restrict__ pairs, int64_t k, int vec,
+        uint8_t* __restrict__ out, int ovec, DevState* __restrict__ ds) {
+    const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
+    if (e0 >= k) return;
+    int u[E], v[E];
+    load_pairs<E>(pairs, e0, k, vec, u, v);
+    bool ok[E];
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        ok[i] = e0 + i < k;
+        if (ok[i] && !(in_range(u[i], n) && in_range(v[i], n))) {
+            ok[i] = false;
+            bad = true;
+        }
+        if (!ok[i]) { u[i] = 0; v[i] = 0; }
+    }
+    int pu[E], pv[E];
+    uint8_t a[E];
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        if (MODE == 1) {
+            pu[i] = parent[u[i]];
+            pv[i] = parent[v[i]];
+        } else {
+            pu[i] = __ldg(parent + u[i]);
+            pv[i] = __ldg(parent + v[i]);
+        }
+    }
+    if (MODE == 2) {
+#pragma unroll
+        for (int i = 0; i < E; i++) a[i] = (uint8_t)(ok[i] && pu[i] == pv[i]);
+    } else if (MODE == 1) {
+#pragma unroll
+        for (int i = 0; i < E; i++) {
+            if (!ok[i]) { a[i] = 0; continue; }
+            if (pu[i] == pv[i]) { a[i] = 1; continue; }
+            int ru = pu[i] == u[i] ? u[i] : find_from(parent, u[i], pu[i], ds);
+            int rv = pv[i] == v[i] ? v[i] : find_from(parent, v[i], pv[i], ds);
+            a[i] = (uint8_t)(ru == rv);
+        }
+    } else {
+        // walk state: x = current node, p = its parent; done when p >= x
+        int x[2 * E], p[2 * E];
+#pragma unroll
+        for (int i = 0; i < E; i++) {
+            bool live = ok[i] && pu[i] != pv[i];
+            x[2 * i] = u[i];     p[2 * i] = live ? pu[i] : u[i];
+            x[2 * i + 1] = v[i]; p[2 * i + 1] = live ? pv[i] : v[i];
+        }
+        while (true) {
+            bool any = false;
+#pragma unroll
+            for (int c = 0; c < 2 * E; c++) {
+                if (p[c] < x[c]) {
+                    x[c] = p[c];
+                    p[c] = __ldg(parent + x[c]);
+                    any = true;
+                }
+            }
+            if (!any) break;
+        }
+#pragma unroll
+        for (int i = 0; i < E; i++) {
+            if (p[2 * i] > x[2 * i] || p[2 * i + 1] > x[2 * i + 1]) flag(ds, ST_CORRUPT);
+            a[i] = (uint8_t)(ok[i] && (pu[i] == pv[i] || x[2 * i] == x[2 * i + 1]));
+        }
+    }
+    store_answers<E>(out, e0, k, ovec != 0, a);
+    if (bad) flag(ds, ST_RANGE);
+}
+
+template <int MODE>
+static void query_inst(unsigned g, Launch cfg, cudaStream_t s, int* parent, int n,
+                       const int* pairs, int64_t k, int vec, uint8_t* out, int ovec, DevState* ds) {
+    switch (cfg.ept) {
+        case 1: k_query<1, MODE><<<g, cfg.block, 0, s>>>(parent, n, pairs, k, vec, out, ovec, ds); break;
+        case 2: k_query<2, MODE><<<g, cfg.block, 0, s>>>(parent, n, pairs, k, vec, out, ovec, ds); break;
+        default: k_query<4, MODE><<<g, cfg.block, 0, s>>>(parent, n, pairs, k, vec, out, ovec, ds); break;
+    }
+}
+
+cudaError_t launch_query(int* parent, int n, const int* pairs, int64_t k, uint8_t* out,
+                         DevState* ds, int mode, Launch cfg, cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    const int vec = pair_vec(pairs);
+    const int ovec = (reinterpret_cast<uintptr_t>(out) % cfg.ept) == 0;
+    const unsigned g = blocks_for(k, (int64_t)cfg.ept * cfg.block);
+    if (mode == 2) query_inst<2>(g, cfg, s, parent, n, pairs, k, vec, out, ovec, ds);
+    else if (mode == 1) query_inst<1>(g, cfg, s, parent, n, pairs, k, vec, out, ovec, ds);
+    else query_inst<0>(g, cfg, s, parent, n, pairs, k, vec, out, ovec, ds);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ compression
+
+// Every vertex is pointed at its root (4 consecutive vertices per thread, one
+// 16-byte read of their parents; the four walks advance in lockstep). Only
+// entries that change are written. With OUT, the roots are also written to
+// out[] -- the minimum-id labels, since the root is the smallest id of its
+// tree. No hooks run concurrently, so the roots are fixed for the whole pass.
+template <bool OUT>
+__global__ void __launch_bounds__(1024)
+k_compress_all(int* __restrict__ parent, int64_t n, int* __restrict__ out,
+               DevState* __restrict__ ds) {
+    const int64_t v0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (v0 >= n) return;
+    const bool full = v0 + 4 <= n;
+    int p0[4], x[4], p[4];
+    if (full) {
+        int4 q = *reinterpret_cast<const int4*>(parent + v0);
+        p0[0] = q.x; p0[1] = q.y; p0[2] = q.z; p0[3] = q.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; i++) p0[i] = v0 + i < n ? parent[v0 + i] : (int)(v0 + i);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        x[i] = (int)(v0 + i);
+        p[i] = p0[i];
+    }
+    while (true) {
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            if (p[i] < x[i]) {
+                x[i] = p[i];
+                p[i] = parent[x[i]];
+                any = true;
+            }
+        }
+        if (!any) break;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        if (p[i] > x[i]) flag(ds, ST_CORRUPT);
+        if (v0 + i < n && x[i] != p0[i]) parent[v0 + i] = x[i];
+    }
+    if (OUT) {
+        if (full) {
+            reinterpret_cast<int4*>(out)[v0 / 4] = make_int4(x[0], x[1], x[2], x[3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                if (v0 + i < n) out[v0 + i] = x[i];
+        }
+    }
+}
+
+cudaError_t launch_compress_all(int* parent, int64_t n, int* out, DevState* ds, int block,
+                                cudaStream_t s) {
+    const unsigned g = blocks_for(n, 4LL * block);
+    const bool aligned_out = out && reinterpret_cast<uintptr_t>(out) % 16 == 0;
+    if (out && !aligned_out) {
+        // labels into a buffer without 16-byte alignment: compress, then copy
+        k_compress_all<false><<<g, block, 0, s>>>(parent, n, nullptr, ds);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return cudaMemcpyAsync(out, parent, (size_t)n * sizeof(int), cudaMemcpyDeviceToDevice, s);
+    }
+    if (out) k_compress_all<true><<<g, block, 0, s>>>(parent, n, out, ds);
+    else k_compress_all<false><<<g, block, 0, s>>>(parent, n, nullptr, ds);
+    return cudaGetLastError();
+}
+
+// Section 5.1's pragmatic compression for the endpoints of an edge array:
+// find the root, then walk the path again pointing every node at it.
+template <int E>
+__global__ void __launch_bounds__(1024)
+k_compress_touched(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k,
+                   int vec, DevState* __restrict__ ds) {
+    const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
+    if (e0 >= k) return;
+    int u[E], v[E];
+    load_pairs<E>(edges, e0, k, vec, u, v);
+#pragma unroll
+    for (int j = 0; j < 2 * E; j++) {
+        const int i = j >> 1;
+        int x = (j & 1) ? v[i] : u[i];
+        if (e0 + i >= k || !in_range(x, n)) continue;
+        int p = parent[x];
+        if (p >= x) continue;
+        const int r = walk_root(parent, x, p);
+        while (p != r && p < x) {
+            parent[x] = r;
+            x = p;
+            p = parent[x];
+        }
+    }
+}
+
+cudaError_t launch_compress_touched(int* parent, int n, const int* edges, int64_t k,
+                                    DevState* ds, Launch cfg, cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    const int vec = pair_vec(edges);
+    const unsigned g = blocks_for(k, (int64_t)cfg.ept * cfg.block);
+    switch (cfg.ept) {
+        case 1: k_compress_touched<1><<<g, cfg.block, 0, s>>>(parent, n, edges, k, vec, ds); break;
+        case 2: k_compress_touched<2><<<g, cfg.block, 0, s>>>(parent, n, edges, k, vec, ds); break;
+        default: k_compress_touched<4><<<g, cfg.block, 0, s>>>(parent, n, edges, k, vec, ds); break;
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- label validation
+
+__global__ void __launch_bounds__(1024)
+k_validate_labels(const int* __restrict__ lab, int64_t n, DevState* __restrict__ ds) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int root = 0;
+    if (v < n) {
+        const int l = lab[v];
+        const bool good = l >= 0 && (int64_t)l <= v && lab[l] == l;
+        if (!good) atomicOr(&ds->labels_bad, 1u);
+        root = good && (int64_t)l == v;
+    }
+    root = __reduce_add_sync(0xffffffffu, root);
+    if ((threadIdx.x & 31) == 0 && root) atomicAdd(&ds->roots, (unsigned long long)root);
+}
+
+cudaError_t launch_validate_labels(const int* lab, int64_t n, DevState* ds, int block,
+                                   cudaStream_t s) {
+    k_validate_labels<<<blocks_for(n, block), block, 0, s>>>(lab, n, ds);
+    return cudaGetLastError();
+}
+
+}  // namespace cc

@@ -1,0 +1,269 @@
+"""CUDA path (through the C-ABI) against the CPU oracle: bit-exact answers,
+minimum-id labels and component counts, on seeded streams, edge cases, and
+the full-size R-MAT and grid streams in the benchmark's launch configuration.
+
+Parent forests are not unique (link rules differ), so parity is checked on
+what is: every query answer and every canonical label. Forest invariants
+(parent[v] <= v, entries never increase, roots are component minima) are
+checked on the raw parent array.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1602_05232_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+OPTION_SETS = {
+    "default": {},
+    "ept1_b64": {"edges_per_thread": 1, "block": 64},
+    "ept4_b1024": {"edges_per_thread": 4, "block": 1024},
+    "no_compress": {"compress_every": 0},
+    "no_compress_halving_query": {"compress_every": 0, "query_halving": 1},
+    "touched_compress": {"compress_scope": 1},
+    "compress_every3": {"compress_every": 3},
+}
+
+
+@pytest.fixture(scope="module")
+def cc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1602_05232_gb300 import _build, cc as ccmod
+    _build.build_cc()
+    ccmod.load()
+    return ccmod
+
+
+def dev(a: np.ndarray) -> torch.Tensor:
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_stream(cc, stream, options, label_every=1, check_invariants=False):
+    f = cc.Forest(stream.n, **options)
+    ref = oracle.OracleUF(stream.n)
+    prev_parent = None
+    for i, (e, q) in enumerate(stream):
+        f.bulk_update(dev(e))
+        got = f.bulk_query(dev(q)).cpu().numpy()
+        ref.bulk_update(e)
+        want = ref.bulk_query(q)
+        assert np.array_equal(got, want), f"answers differ at batch {i}: " \
+            f"{int((got != want).sum())} of {len(want)}"
+        if check_invariants:
+            par = f.parent().cpu().numpy()
+            assert np.all(par <= np.arange(stream.n)), "parent[v] > v"
+            if prev_parent is not None:
+                assert np.all(par <= prev_parent), "a parent entry increased"
+            prev_parent = par
+        if label_every and (i % label_every == 0 or i == stream.batches - 1):
+            lab = f.labels().cpu().numpy()
+            assert np.array_equal(lab, ref.labels()), f"labels differ at batch {i}"
+            assert f.components() == ref.components, f"components differ at batch {i}"
+            if check_invariants:
+                par = f.parent().cpu().numpy()
+                roots = np.flatnonzero(par == np.arange(stream.n))
+                assert np.array_equal(lab[roots], roots), "a root is not its component minimum"
+    f.sync()
+    f.close()
+    return ref
+
+
+@pytest.mark.parametrize("opts", list(OPTION_SETS), ids=list(OPTION_SETS))
+def test_uniform_small_every_batch(cc, opts):
+    # n = 2^16, 16 minibatches of 2^16 uniform edges, 2^16 queries after each
+    run_stream(cc, I.uniform_stream(), OPTION_SETS[opts], label_every=1,
+               check_invariants=(opts == "default"))
+
+
+@pytest.mark.parametrize("opts", ["default", "ept1_b64", "no_compress", "touched_compress"])
+def test_rmat_small(cc, opts):
+    s = I.rmat_stream(scale=16, m=1 << 20, batch=(1 << 16) + 3, q=(1 << 16) - 5, seed=1)
+    run_stream(cc, s, OPTION_SETS[opts], label_every=4, check_invariants=True)
+
+
+@pytest.mark.parametrize("opts", ["default", "no_compress", "ept4_b1024", "compress_every3"])
+def test_grid_small(cc, opts):
+    s = I.grid_stream(512, 512, batch=(1 << 14) + 1, q=1 << 14, seed=2)
+    ref = run_stream(cc, s, OPTION_SETS[opts], label_every=8, check_invariants=True)
+    assert ref.components == 1
+
+
+def test_edge_cases(cc):
+    n = 1000
+    f = cc.Forest(n)
+    ref = oracle.OracleUF(n)
+
+    def both(e):
+        e = np.asarray(e, dtype=np.int32).reshape(-1, 2)
+        f.bulk_update(dev(e))
+        ref.bulk_update(e)
+
+    both(np.zeros((0, 2)))                       # empty minibatch
+    both([[5, 9]])                               # k = 1
+    both([[1, 2], [3, 4], [5, 6]])               # odd k
+    both([[7, 7]] * 17)                          # only self-loops
+    both([[10, 11]] * 33 + [[11, 10]] * 31)      # duplicates both ways
+    both([[999, i] for i in range(100, 400)])    # star into a high-id hub
+    both([[0, i] for i in range(400, 700)])      # star into a low-id hub
+    both([[i, i - 1] for i in range(999, 900, -1)])  # descending path
+    q = np.random.default_rng(0).integers(0, n, size=(20000, 2)).astype(np.int32)
+    assert np.array_equal(f.bulk_query(dev(q)).cpu().numpy(), ref.bulk_query(q))
+    assert np.array_equal(f.labels().cpu().numpy(), ref.labels())
+    assert f.components() == ref.components
+    empty = f.bulk_query(dev(np.zeros((0, 2), dtype=np.int32)))
+    assert empty.numel() == 0
+    f.sync()
+
+
+def test_unaligned_arrays(cc):
+    # pair arrays starting 8 and 4 bytes past a 16-byte boundary, odd lengths
+    s = I.uniform_stream(n=5000, m=40001, batch=40001, q=30001, seed=3)
+    e, q = s.edges(0), s.queries(0)
+    ref = oracle.OracleUF(s.n)
+    ref.bulk_update(e)
+    want = ref.bulk_query(q)
+    for shift in (2, 1):   # in int32 elements: 8 bytes, 4 bytes
+        for ept in (1, 2, 4):
+            f = cc.Forest(s.n, edges_per_thread=ept)
+            buf = torch.zeros(e.size + 4, dtype=torch.int32, device="cuda")
+            buf[shift:shift + e.size] = dev(e.ravel())
+            f.bulk_update(buf[shift:shift + e.size])
+            qb = torch.zeros(q.size + 4, dtype=torch.int32, device="cuda")
+            qb[shift:shift + q.size] = dev(q.ravel())
+            out = torch.zeros(len(q) + 3, dtype=torch.uint8, device="cuda")
+            f.bulk_query(qb[shift:shift + q.size], out=out[1:1 + len(q)])
+            assert np.array_equal(out[1:1 + len(q)].cpu().numpy(), want), (shift, ept)
+            lab = torch.zeros(s.n + 1, dtype=torch.int32, device="cuda")
+            f.labels(out=lab[1:])
+            assert np.array_equal(lab[1:].cpu().numpy(), ref.labels())
+            f.sync()
+
+
+def test_out_of_range_ids(cc):
+    n = 100
+    f = cc.Forest(n)
+    ref = oracle.OracleUF(n)
+    e = np.array([[0, 1], [-1, 2], [2, n], [3, 4], [2**31 - 1, 5], [5, 6]], dtype=np.int32)
+    f.bulk_update(dev(e))
+    ref.bulk_update(e)
+    with pytest.raises(cc.CCError) as ex:
+        f.sync()
+    assert ex.value.status == cc.CC_ERR_RANGE
+    f.sync()  # the status word was cleared
+    assert np.array_equal(f.labels().cpu().numpy(), ref.labels())
+    q = np.array([[0, 1], [n, n], [-5, 0], [3, 4]], dtype=np.int32)
+    assert f.bulk_query(dev(q)).cpu().numpy().tolist() == ref.bulk_query(q).tolist() == [1, 0, 0, 1]
+    with pytest.raises(cc.CCError):
+        f.sync()
+
+
+def test_argument_errors_leave_state(cc):
+    f = cc.Forest(10)
+    with pytest.raises(TypeError):
+        f.bulk_update(torch.zeros(4, dtype=torch.int64, device="cuda"))
+    with pytest.raises(cc.CCError) as ex:
+        f.set_option("block", 100)
+    assert ex.value.status == cc.CC_ERR_ARG
+    with pytest.raises(cc.CCError):
+        f.set_option("edges_per_thread", 3)
+    assert f.get_option("block") == 256
+    assert f.components() == 10
+
+
+def test_checkpoint_resume(cc):
+    s = I.rmat_stream(scale=14, m=1 << 17, batch=1 << 13, q=1 << 12, seed=4)
+    whole = cc.Forest(s.n)
+    first = cc.Forest(s.n)
+    cut = 7
+    for i, (e, q) in enumerate(s):
+        whole.bulk_update(dev(e))
+        if i < cut:
+            first.bulk_update(dev(e))
+    saved = first.labels()
+    resumed = cc.Forest(s.n)
+    resumed.load_labels(saved)
+    assert resumed.components() == first.components()
+    for i in range(cut, s.batches):
+        resumed.bulk_update(dev(s.edges(i)))
+    assert torch.equal(resumed.labels(), whole.labels())
+    assert resumed.components() == whole.components()
+    q = dev(s.all_queries())
+    assert torch.equal(resumed.bulk_query(q), whole.bulk_query(q))
+    # an invalid labelling is refused and the forest is left as it was
+    before = resumed.labels().clone()
+    bad = before.clone()
+    bad[5] = 7   # label above the vertex id
+    with pytest.raises(cc.CCError) as ex:
+        resumed.load_labels(bad)
+    assert ex.value.status == cc.CC_ERR_LABELS
+    assert torch.equal(resumed.labels(), before)
+
+
+def test_non_default_stream_and_touched_compress_api(cc):
+    st = torch.cuda.Stream()
+    s = I.uniform_stream(n=1 << 14, m=1 << 16, batch=1 << 13, q=1 << 13, seed=5)
+    ref = oracle.OracleUF(s.n)
+    with torch.cuda.stream(st):
+        f = cc.Forest(s.n, compress_every=0)
+        for e, q in s:
+            de, dq = dev(e), dev(q)
+            f.bulk_update(de)
+            f.compress("touched", de)
+            got = f.bulk_query(dq)
+            ref.bulk_update(e)
+            assert np.array_equal(got.cpu().numpy(), ref.bulk_query(q))
+        f.compress("all")
+        assert np.array_equal(f.labels().cpu().numpy(), ref.labels())
+    st.synchronize()
+
+
+def test_kernel_counters_and_profile(cc):
+    f = cc.Forest(1 << 12, profile=1)
+    e = dev(I.uniform_pairs(1 << 12, 5000, seed=0, tag=1))
+    f.bulk_update(e)
+    f.bulk_query(e)
+    st = f.kernel_stats(timing=True)
+    assert st["update"][0] == 1 and st["compress_all"][0] == 1 and st["query"][0] == 1
+    assert st["update"][1] > 0 and st["query"][1] > 0
+
+
+# ----------------------------------------------------------- full sizes
+
+def _full_stream(cc, s, options, label_batches):
+    """Whole stream through the GPU and the oracle; every answer compared."""
+    f = cc.Forest(s.n, **options)
+    ref = oracle.OracleUF(s.n)
+    for i in range(s.batches):
+        e, q = s.edges(i), s.queries(i)
+        f.bulk_update(dev(e))
+        got = f.bulk_query(dev(q))
+        ref.bulk_update(e)
+        want = ref.bulk_query(q)
+        assert np.array_equal(got.cpu().numpy(), want), f"answers differ at batch {i}"
+        if i in label_batches:
+            assert np.array_equal(f.labels().cpu().numpy(), ref.labels()), f"labels at {i}"
+    f.sync()
+    return f, ref
+
+
+def test_full_size_rmat_stream(cc):
+    # R-MAT scale 24 (n = 2^24), 2^27 edges in 128 minibatches of 2^20, 2^20
+    # queries after each: every answer and the final labels against the oracle
+    from bench import launch_options
+    s = I.rmat_stream()
+    f, ref = _full_stream(cc, s, launch_options("rmat"), label_batches={0, 63, s.batches - 1})
+    assert f.components() == ref.components
+
+
+def test_full_size_grid_stream(cc):
+    # 8192 x 8192 grid, shuffled, minibatches of 2^22 with 2^22 queries each
+    from bench import launch_options
+    s = I.grid_stream()
+    f, ref = _full_stream(cc, s, launch_options("grid"), label_batches={0, s.batches // 2})
+    lab = f.labels()
+    assert int(lab.max()) == 0 and f.components() == 1 == ref.components
