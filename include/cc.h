@@ -180,6 +180,37 @@ cc_status cc_get_option(const cc_ctx* ctx, int32_t option, int64_t* value);
  * timing sums, not the counters. */
 cc_status cc_kernel_stats(cc_ctx* ctx, uint64_t* launches, double* ms);
 
+/* ------------------------------------------- allocation-free labelling */
+
+/* The paper has no counterpart to this entry point: it exists for callers
+ * that cannot allocate device memory. Examples are code whose stream is being
+ * captured into a CUDA graph, real-time loops that cannot afford cudaMalloc's
+ * implicit synchronisation, and plugins whose host framework owns all device
+ * memory.
+ *
+ * Computes labels[v] = the smallest vertex id connected to v in the graph of
+ * the k edges at `edges` on vertices 0..n-1: one Bulk-Update of a fresh
+ * forest, then a full compression. The working forest and status word live
+ * in a static device array inside libcc of CC_STATIC_MAX_VERTICES vertices
+ * (16 MiB); every GPU that loads libcc holds it until the process exits. No
+ * call allocates.
+ *
+ * `edges` (device, 2k int32) and `labels` (device, n int32) are caller-owned.
+ * `status` (device, one uint32, may be NULL) receives the kernels' status
+ * bits: 1 = an id outside [0, n) was skipped. Asynchronous on `stream`.
+ *
+ * All calls share the static array and each call re-initialises it, so calls
+ * whose work can overlap on the GPU (e.g. on two unordered streams) race and
+ * give wrong labels: order them. The first call on each device looks up the
+ * array's device address; make that first call before any stream capture.
+ *
+ * Errors: CC_ERR_ARG if n < 1 or n > CC_STATIC_MAX_VERTICES, or for bad k or
+ * pointers, with nothing enqueued; CC_ERR_CUDA if the lookup or a launch
+ * fails. */
+#define CC_STATIC_MAX_VERTICES (1 << 22)
+cc_status cc_components_static(const int32_t* edges, int64_t k, int64_t n, int32_t* labels,
+                               uint32_t* status, cc_stream_t stream);
+
 int64_t cc_num_vertices(const cc_ctx* ctx);
 const char* cc_status_string(cc_status s);
 const char* cc_last_error_string(void);

@@ -128,6 +128,11 @@ cc_status do_compress(cc_ctx* c, int scope, const int32_t* edges, int64_t k) {
 
 }  // namespace
 
+namespace cc {
+// Lets the other translation units leave a message for cc_last_error_string().
+cc_status record_error(cc_status s, const char* msg) { return fail(s, "%s", msg); }
+}  // namespace cc
+
 #define CC_CHECK_CTX(c)                                            \
     do {                                                           \
         if (!(c)) return fail(CC_ERR_ARG, "null cc_ctx handle");   \

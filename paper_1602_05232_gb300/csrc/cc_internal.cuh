@@ -30,6 +30,9 @@ struct Launch {
 // Alignment class of a pair array: 2 = 16-byte, 1 = 8-byte, 0 = 4-byte.
 int pair_vec(const void* p);
 
+// Sets the text returned by cc_last_error_string() and returns s.
+cc_status record_error(cc_status s, const char* msg);
+
 cudaError_t launch_reset(int* parent, int64_t n, int block, cudaStream_t s);
 
 cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevState* ds,
