@@ -43,9 +43,14 @@ BYTES_PER_UNIT = {"update": 72.0, "query": 73.0, "compress_all": 8.0,
 # Options of the launches this benchmark times, per workload (also used by
 # the full-size parity tests, so they check exactly this configuration).
 LAUNCH_OPTIONS = {
-    "rmat": {"block": 256, "edges_per_thread": 2, "compress_every": 1, "compress_scope": 0},
-    "uniform": {"block": 256, "edges_per_thread": 2, "compress_every": 1, "compress_scope": 0},
-    "grid": {"block": 256, "edges_per_thread": 2, "compress_every": 1, "compress_scope": 0},
+    "rmat": {"block": 256, "edges_per_thread": 4, "update_variant": 2, "compress_every": 0,
+             "compress_scope": 0},
+    "uniform": {"block": 256, "edges_per_thread": 2, "update_variant": 0, "compress_every": 0,
+                "compress_scope": 0},
+    "grid": {"block": 256, "edges_per_thread": 2, "update_variant": 2, "compress_every": 4,
+             "compress_scope": 0},
+    "segmented": {"seg_block": 512, "seg_edges_per_thread": 1, "seg_smem_cap": 65536,
+                  "seg_graph": 1},
 }
 
 
@@ -71,6 +76,8 @@ WORKLOAD_TEXT = {
                "a Bulk-Query of 2^16 uniform pairs",
     "grid": "shuffled 8192x8192 4-neighbour grid (n=2^26, 134,201,344 edges) in 32 "
             "Bulk-Updates of 2^22, each followed by a Bulk-Query of 2^22 uniform pairs",
+    "segmented": "1024 graphs, n log-uniform in [2^8,2^16), m=4n uniform edges, minibatches "
+                 "log-uniform in [2^6,2^14), each followed by a Bulk-Query of the same size",
 }
 
 
@@ -194,6 +201,113 @@ def ncu_traffic(kernel: str, workload: str):
         return ent["bytes_per_launch"] if ent.get("source_hash") == h else None
     except Exception:
         return None
+
+
+# ------------------------------------------------------ batched form (segmented)
+
+def run_segmented(args, rank: int, world: int, local_rank: int, dist) -> dict:
+    """Many graphs: a STEP is the whole workload (every graph's minibatch
+    stream) from an empty forest, as ONE cc_submit (persistent kernel,
+    replayed CUDA graph), against the plain form: the same minibatches as one
+    launch each on a plain handle with global ids."""
+    import torch
+    from paper_1602_05232_gb300 import cc, inputs as I
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = I.segmented_workload(seed=rank)
+    off = np.concatenate([[0], np.cumsum(w.n)]).astype(np.int64)
+    m_all = int(w.total_edges)
+    h_e = np.empty((m_all, 2), dtype=np.int32)
+    h_q = np.empty((m_all, 2), dtype=np.int32)
+    eoff = np.concatenate([[0], np.cumsum([w.m(g) for g in range(w.G)])]).astype(np.int64)
+    for g in range(w.G):
+        h_e[eoff[g]:eoff[g + 1]] = w.edges(g)
+        h_q[eoff[g]:eoff[g + 1]] = w.queries(g)
+    d_e = torch.from_numpy(h_e).to(dev)
+    d_q = torch.from_numpy(h_q).to(dev)
+    shift = torch.from_numpy(np.repeat(off[:-1], [w.m(g) for g in range(w.G)]).astype(np.int32)).to(dev)
+    d_eg = d_e + shift[:, None]          # global ids for the plain form
+    d_qg = d_q + shift[:, None]
+    out = torch.empty(m_all, dtype=torch.uint8, device=dev)
+    seq = []
+    for g in range(w.G):
+        for kind, o, k in w.ops(g):
+            seq.append((g, kind, int(eoff[g]) + o, k))
+    ops = np.zeros(len(seq), dtype=cc.OP_DTYPE)
+    for i, (g, kind, o, k) in enumerate(seq):
+        ops[i] = (g, kind, (d_e if kind == 0 else d_q).data_ptr() + 8 * o, k,
+                  out.data_ptr() + o if kind == 1 else 0)
+    stream = torch.cuda.Stream(device=dev)
+    opts = launch_options("segmented")
+    with torch.cuda.stream(stream):
+        f = cc.Forest.segmented(w.n, stream=stream, **opts)
+        for _ in range(args.warmup):
+            f.reset()
+            f.submit(ops)
+        stream.synchronize()
+        f.set_option("profile", 1)
+        f.kernel_stats(timing=True)
+        l0 = f.kernel_stats()
+        dist_barrier(dist)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local_rank) as clk:
+            a.record(stream)
+            for _ in range(args.steps):
+                f.reset()
+                f.submit(ops)
+            b.record(stream)
+            stream.synchronize()
+        dist_barrier(dist)
+        ks = f.kernel_stats(timing=True)
+        l1 = f.kernel_stats()
+        f.sync()
+        f.close()
+        ms = dist_max(dist, a.elapsed_time(b), dev)
+        # plain form: one launch per minibatch, same edges with global ids
+        fp = cc.Forest(int(off[-1]), stream=stream, **launch_options("uniform"))
+        plain_steps = max(1, min(args.steps, 2))
+
+        def plain_pass():
+            fp.reset()
+            for g, kind, o, k in seq:
+                if kind == 0:
+                    fp.bulk_update(d_eg[o:o + k])
+                else:
+                    fp.bulk_query(d_qg[o:o + k], out=out[o:o + k])
+        plain_pass()
+        stream.synchronize()
+        a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a2.record(stream)
+        for _ in range(plain_steps):
+            plain_pass()
+        b2.record(stream)
+        stream.synchronize()
+        pl = fp.kernel_stats()
+        fp.sync()
+        fp.close()
+    ms_plain = a2.elapsed_time(b2) / plain_steps
+    edges_all = dist_sum(dist, float(m_all * args.steps), dev)
+    value = edges_all / (ms / 1e3)
+    seg_ms = ks["segmented"][1] / max(1, l1["segmented"] - l0["segmented"])
+    return {
+        "metric": METRIC, "value": round(value, 1), "unit": "edges/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "form": "batched",
+        "config": {"workload": WORKLOAD_TEXT["segmented"], "graphs": w.G,
+                   "vertices": int(off[-1]), "edges": m_all, "queries": m_all,
+                   "ops_per_step": len(ops), "options": opts},
+        "queries_per_s": round(edges_all / (ms / 1e3), 1),
+        "kernel_ms_per_submit": round(seg_ms, 4),
+        "gpu_launches": sum(l1[k] - l0[k] for k in l1),
+        "plain_form": {"edges_per_s": round(m_all / (ms_plain / 1e3), 1),
+                       "ms_per_pass": round(ms_plain, 3),
+                       "launches_per_pass": len(seq), "what": "one cc_bulk_update / "
+                       "cc_bulk_query launch per minibatch on a plain handle, global ids"},
+        "speedup_vs_plain": round(ms_plain / (ms / args.steps), 2),
+        "clocks": clk.summary(),
+    }
 
 
 # --------------------------------------------------------------- GPU arm
@@ -486,7 +600,10 @@ def main(argv=None) -> int:
         out = run_reference(args, rank, world)
     else:
         dist = dist_init(world, "nccl")
-        out = run_gpu(args, rank, world, local_rank, dist)
+        if args.workload == "segmented":
+            out = run_segmented(args, rank, world, local_rank, dist)
+        else:
+            out = run_gpu(args, rank, world, local_rank, dist)
         if dist is not None:
             dist.destroy_process_group()
     if rank == 0 and out is not None:

@@ -72,7 +72,21 @@ typedef enum {
     CC_OPT_COMPRESS_SCOPE = 3,   /* scope of that automatic compression: a cc_compress_scope (default ALL) */
     CC_OPT_QUERY_HALVING = 4,    /* 1: Bulk-Query finds also halve paths (they write); 0: read-only finds (default) */
     CC_OPT_PROFILE = 5,          /* 1: time every kernel with CUDA events on the handle's stream */
-    CC_OPT__COUNT = 6
+    CC_OPT_UPDATE_VARIANT = 6,   /* Bulk-Update kernel: 0 per-edge walks, 1 lockstep walks of all
+                                    endpoints of a thread, 2 = 1 on a persistent grid that prefetches
+                                    the next edges (default 0) */
+    CC_OPT_L2_PERSIST = 7,       /* 1: ask L2 to keep the forest resident (an access-policy window
+                                    set on the handle's stream around each kernel; the process's
+                                    persisting-L2 limit is raised to the forest size, capped by the
+                                    device maximum). Best effort; default 0 */
+    CC_OPT_SEG_BLOCK = 8,        /* batched form: threads per CTA of the persistent kernel (default 512) */
+    CC_OPT_SEG_EDGES_PER_THREAD = 9, /* batched form: edges (pairs) per thread per step: 1, 2, 4 (default 1) */
+    CC_OPT_SEG_SMEM_CAP = 10,    /* batched form: graphs of at most this many vertices are processed in
+                                    shared memory (0..65536; default 65536; 0 = all in global memory) */
+    CC_OPT_SEG_GRAPH = 11,       /* batched form: 1 = capture the submit (table copy, queue reset,
+                                    kernel) once as a CUDA graph and replay it (default 1) */
+    CC_OPT_SEG_MAX_CTAS = 12,    /* batched form: cap on persistent CTAs (0 = one full wave, default) */
+    CC_OPT__COUNT = 13
 } cc_option;
 
 /* Kernel kinds reported by the launch counters and the profiler. */
@@ -167,6 +181,45 @@ cc_status cc_copy_parent(cc_ctx* ctx, int32_t* out);
 /* Number of connected components (n minus the successful hooks since create
  * or reset). Synchronises; *out is a host int64. */
 cc_status cc_components(cc_ctx* ctx, int64_t* out);
+
+/* ---------------------------------------- batched form (many graphs) */
+
+/* Many independent graphs in one handle (the batching pattern: uneven
+ * minibatches, Section 1, over many small graphs). Graph g has n_per_graph[g]
+ * vertices with LOCAL ids 0..n_g-1; it owns the slice [off_g, off_g + n_g)
+ * of one forest, off_g = n_0 + ... + n_{g-1}. `n_per_graph` is a host array
+ * of G values, each >= 1, summing to at most 2^31 - 1. On such a handle (G >
+ * 1) the forest changes only through cc_submit and cc_reset, so no edge ever
+ * joins two graphs: cc_bulk_update, touched compression and cc_load_labels
+ * return CC_ERR_UNSUPPORTED. Bulk-Query, cc_labels and cc_components take
+ * GLOBAL ids (off_g + local id); labels are global minimum ids. */
+cc_status cc_create_segmented(int32_t G, const int64_t* n_per_graph, cc_ctx** out);
+
+enum { CC_OP_UPDATE = 0, CC_OP_QUERY = 1 };
+
+/* One bulk operation of the batched form. */
+typedef struct {
+    int32_t graph;        /* graph index in [0, G) (0 on a handle from cc_create) */
+    int32_t kind;         /* CC_OP_UPDATE (Algorithm 2) or CC_OP_QUERY (Algorithm 1) */
+    const int32_t* data;  /* device: 2k int32 local ids, u0 v0 u1 v1 ... (4-byte aligned) */
+    int64_t k;            /* edges or pairs, 0 <= k <= 2^31 - 1 */
+    uint8_t* out;         /* device: k answers (CC_OP_QUERY), else ignored */
+} cc_op;
+
+/* Run `nops` operations (host array) in ONE persistent kernel launch. The
+ * operations of one graph run in their order in `ops`, each completing before
+ * the next starts (Section 1); operations of different graphs are independent.
+ * A CTA takes a whole graph (largest work first), loads its slice of the
+ * forest into shared memory when it has at most CC_OPT_SEG_SMEM_CAP vertices,
+ * runs its operations there with the same find/hook as the plain path, and
+ * writes the slice back with every vertex pointing at its root. With
+ * CC_OPT_SEG_GRAPH the table copy, the queue reset and the launch are
+ * captured once as a CUDA graph and replayed on later calls. The library
+ * copies `ops` into pinned staging memory, so `ops` may be reused on return;
+ * the data/out arrays must stay valid until the stream reaches the call.
+ * Errors: CC_ERR_ARG (bad graph, kind, k or pointer) before anything is
+ * enqueued; out-of-range local ids are reported by cc_sync (CC_ERR_RANGE). */
+cc_status cc_submit(cc_ctx* ctx, const cc_op* ops, int64_t nops);
 
 /* ----------------------------------------------------------- tunables */
 

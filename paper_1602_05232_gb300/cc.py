@@ -11,6 +11,7 @@ from __future__ import annotations
 import ctypes
 from pathlib import Path
 
+import numpy as np
 import torch
 
 from ._build import LIBCC
@@ -19,10 +20,17 @@ CC_OK, CC_ERR_ARG, CC_ERR_OOM, CC_ERR_CUDA, CC_ERR_RANGE, CC_ERR_CORRUPT, CC_ERR
     CC_ERR_UNSUPPORTED = range(8)
 COMPRESS_ALL, COMPRESS_TOUCHED = 0, 1
 OPT_BLOCK, OPT_EDGES_PER_THREAD, OPT_COMPRESS_EVERY, OPT_COMPRESS_SCOPE, OPT_QUERY_HALVING, \
-    OPT_PROFILE = range(6)
+    OPT_PROFILE, OPT_UPDATE_VARIANT, OPT_L2_PERSIST = range(8)
 OPTIONS = {"block": OPT_BLOCK, "edges_per_thread": OPT_EDGES_PER_THREAD,
            "compress_every": OPT_COMPRESS_EVERY, "compress_scope": OPT_COMPRESS_SCOPE,
-           "query_halving": OPT_QUERY_HALVING, "profile": OPT_PROFILE}
+           "query_halving": OPT_QUERY_HALVING, "profile": OPT_PROFILE,
+           "update_variant": OPT_UPDATE_VARIANT, "l2_persist": OPT_L2_PERSIST,
+           "seg_block": 8, "seg_edges_per_thread": 9, "seg_smem_cap": 10, "seg_graph": 11,
+           "seg_max_ctas": 12}
+OP_UPDATE, OP_QUERY = 0, 1
+# Layout of cc_op (include/cc.h): graph, kind, data pointer, k, out pointer.
+OP_DTYPE = np.dtype([("graph", "<i4"), ("kind", "<i4"), ("data", "<u8"), ("k", "<i8"),
+                     ("out", "<u8")])
 KERNELS = ["update", "compress_all", "compress_touched", "query", "labels", "reset", "load",
            "segmented"]
 
@@ -68,6 +76,8 @@ def load(path: str | Path | None = None) -> ctypes.CDLL:
         "cc_set_option": [vp, i32, i64],
         "cc_get_option": [vp, i32, ctypes.POINTER(ctypes.c_int64)],
         "cc_kernel_stats": [vp, u64p, vp],
+        "cc_create_segmented": [i32, vp, ctypes.POINTER(ctypes.c_void_p)],
+        "cc_submit": [vp, vp, i64],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -112,15 +122,27 @@ class Forest:
     All calls are enqueued on the bound stream (default: the current torch
     stream at construction)."""
 
-    def __init__(self, n: int, stream=None, **options):
+    def __init__(self, n: int, stream=None, _sizes=None, **options):
         self._L = load()
         h = ctypes.c_void_p()
-        check(self._L.cc_create(int(n), ctypes.byref(h)), self._L)
+        if _sizes is None:
+            check(self._L.cc_create(int(n), ctypes.byref(h)), self._L)
+            self.offsets = np.array([0, int(n)], dtype=np.int64)
+        else:
+            sizes = np.ascontiguousarray(_sizes, dtype=np.int64)
+            check(self._L.cc_create_segmented(len(sizes), sizes.ctypes.data, ctypes.byref(h)),
+                  self._L)
+            self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
         self._h = h
-        self.n = int(n)
+        self.n = int(self.offsets[-1])
         self.set_stream(stream)
         for k, v in options.items():
             self.set_option(k, v)
+
+    @classmethod
+    def segmented(cls, n_per_graph, stream=None, **options) -> "Forest":
+        """Many independent graphs (local ids 0..n_g-1) in one handle."""
+        return cls(0, stream=stream, _sizes=n_per_graph, **options)
 
     # lifetime ---------------------------------------------------------
     def close(self) -> None:
@@ -195,6 +217,21 @@ class Forest:
         v = ctypes.c_int64()
         check(self._L.cc_components(self._h, ctypes.byref(v)), self._L)
         return v.value
+
+    def submit(self, ops) -> None:
+        """Run bulk operations in one persistent launch (cc_submit). ``ops`` is
+        an ``OP_DTYPE`` array, or a list of (graph, kind, data, out) with
+        ``data`` an int32 (k, 2) CUDA tensor of local ids and ``out`` a uint8
+        CUDA tensor (queries) or None."""
+        if not isinstance(ops, np.ndarray):
+            arr = np.zeros(len(ops), dtype=OP_DTYPE)
+            for i, (g, kind, data, out) in enumerate(ops):
+                p, k = _pairs_ptr(data, "data")
+                arr[i] = (g, kind, p, k, out.data_ptr() if out is not None else 0)
+            ops = arr
+        if ops.dtype != OP_DTYPE or not ops.flags.c_contiguous:
+            raise TypeError("ops: expected a contiguous OP_DTYPE array")
+        check(self._L.cc_submit(self._h, ops.ctypes.data, len(ops)), self._L)
 
     # tunables and counters ---------------------------------------------
     def set_option(self, name: str, value: int) -> None:

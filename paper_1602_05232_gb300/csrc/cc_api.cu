@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "cc.h"
@@ -49,7 +50,8 @@ struct DeviceScope {
     }
 };
 
-const int64_t kDefaults[CC_OPT__COUNT] = {256, 2, 1, CC_COMPRESS_ALL, 0, 0};
+const int64_t kDefaults[CC_OPT__COUNT] = {256, 2, 1, CC_COMPRESS_ALL, 0, 0, 0, 0,
+                                          512, 1, 65536, 1, 0};
 
 }  // namespace
 
@@ -66,6 +68,23 @@ struct cc_ctx {
     std::vector<cudaEvent_t> spare;
     uint64_t update_calls = 0;
     bool flat = true;  // every tree has height <= 1
+    cudaAccessPolicyWindow window = {};  // L2 window over parent (num_bytes 0 = off)
+
+    // batched form
+    int32_t G = 1;
+    std::vector<int64_t> seg_off_h;  // G + 1 offsets
+    int64_t* seg_off = nullptr;      // device copy
+    int64_t cap_ops = 0;             // capacity of the table buffers, in ops
+    size_t table_bytes = 0;
+    void* staging = nullptr;         // pinned host tables
+    void* tables = nullptr;          // device tables
+    cudaEvent_t staging_free = nullptr;  // recorded after the tables were copied
+    bool staging_pending = false;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_key[5] = {-1, -1, -1, -1, -1};
+    std::vector<int> bucket_count, op_begin_h, order_h;
+    std::vector<int64_t> work_h;
 };
 
 namespace {
@@ -91,8 +110,21 @@ cc_status run(cc_ctx* c, int kind, const char* what, F&& launch) {
         b = take_event(c);
         if (a && b) cudaEventRecord(a, c->stream);
     }
+    const bool window = c->window.num_bytes > 0;
+    if (window) {
+        cudaStreamAttrValue v = {};
+        v.accessPolicyWindow = c->window;
+        if (cudaStreamSetAttribute(c->stream, cudaStreamAttributeAccessPolicyWindow, &v) != cudaSuccess)
+            cudaGetLastError();  // best effort: e.g. the legacy default stream
+    }
     cudaError_t e = launch();
     c->launches[kind]++;
+    if (window) {
+        cudaStreamAttrValue v = {};
+        v.accessPolicyWindow.num_bytes = 0;
+        if (cudaStreamSetAttribute(c->stream, cudaStreamAttributeAccessPolicyWindow, &v) != cudaSuccess)
+            cudaGetLastError();
+    }
     if (a && b) {
         cudaEventRecord(b, c->stream);
         c->pending.push_back({kind, a, b});
@@ -102,7 +134,8 @@ cc_status run(cc_ctx* c, int kind, const char* what, F&& launch) {
 }
 
 cc::Launch cfg_of(const cc_ctx* c) {
-    return cc::Launch{(int)c->opt[CC_OPT_BLOCK], (int)c->opt[CC_OPT_EDGES_PER_THREAD]};
+    return cc::Launch{(int)c->opt[CC_OPT_BLOCK], (int)c->opt[CC_OPT_EDGES_PER_THREAD],
+                      (int)c->opt[CC_OPT_UPDATE_VARIANT]};
 }
 
 cc_status check_pairs(const int32_t* p, int64_t k, const char* name) {
@@ -208,6 +241,12 @@ cc_status cc_destroy(cc_ctx* c) {
             cudaEventDestroy(t.b);
         }
         for (auto ev : c->spare) cudaEventDestroy(ev);
+        if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+        if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+        if (c->staging_free) cudaEventDestroy(c->staging_free);
+        if (c->staging) cudaFreeHost(c->staging);
+        cudaFree(c->tables);
+        cudaFree(c->seg_off);
         cudaFree(c->parent);
         cudaFree(c->ds);
     }
@@ -257,6 +296,7 @@ cc_status cc_bulk_update(cc_ctx* c, const int32_t* edges, int64_t k) {
     CC_CHECK_CTX(c);
     cc_status s = check_pairs(edges, k, "cc_bulk_update");
     if (s != CC_OK) return s;
+    if (c->G > 1) return fail(CC_ERR_UNSUPPORTED, "cc_bulk_update on a segmented handle: use cc_submit");
     if (k == 0) return CC_OK;
     CC_DEVICE(c);
     s = run(c, CC_K_UPDATE, "bulk_update", [&] {
@@ -293,6 +333,7 @@ cc_status cc_compress(cc_ctx* c, int32_t scope, const int32_t* edges, int64_t k)
     if (scope == CC_COMPRESS_TOUCHED) {
         cc_status s = check_pairs(edges, k, "cc_compress");
         if (s != CC_OK) return s;
+        if (c->G > 1) return fail(CC_ERR_UNSUPPORTED, "touched compression on a segmented handle");
     }
     CC_DEVICE(c);
     return do_compress(c, scope, edges, k);
@@ -314,6 +355,7 @@ cc_status cc_load_labels(cc_ctx* c, const int32_t* labels) {
     CC_CHECK_CTX(c);
     if (!labels) return fail(CC_ERR_ARG, "cc_load_labels: labels is null");
     if (reinterpret_cast<uintptr_t>(labels) % 4 != 0) return fail(CC_ERR_ARG, "cc_load_labels: not 4-byte aligned");
+    if (c->G > 1) return fail(CC_ERR_UNSUPPORTED, "cc_load_labels on a segmented handle");
     CC_DEVICE(c);
     cudaError_t e = cudaMemsetAsync(&c->ds->labels_bad, 0, sizeof(unsigned), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&c->ds->roots, 0, sizeof(unsigned long long), c->stream);
@@ -358,6 +400,216 @@ cc_status cc_components(cc_ctx* c, int64_t* out) {
     return CC_OK;
 }
 
+cc_status cc_create_segmented(int32_t G, const int64_t* n_per_graph, cc_ctx** out) {
+    if (!out) return fail(CC_ERR_ARG, "cc_create_segmented: out is null");
+    *out = nullptr;
+    if (G < 1 || !n_per_graph) return fail(CC_ERR_ARG, "cc_create_segmented: need G >= 1 and sizes");
+    std::vector<int64_t> off((size_t)G + 1, 0);
+    for (int32_t g = 0; g < G; g++) {
+        if (n_per_graph[g] < 1) return fail(CC_ERR_ARG, "cc_create_segmented: graph %d has n < 1", g);
+        off[g + 1] = off[g] + n_per_graph[g];
+        if (off[g + 1] > INT32_MAX) return fail(CC_ERR_ARG, "cc_create_segmented: total vertices exceed 2^31-1");
+    }
+    cc_ctx* c = nullptr;
+    cc_status s = cc_create(off[G], &c);
+    if (s != CC_OK) return s;
+    c->G = G;
+    c->seg_off_h = std::move(off);
+    cudaError_t e = cudaMalloc(&c->seg_off, sizeof(int64_t) * (size_t)(G + 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->seg_off, c->seg_off_h.data(), sizeof(int64_t) * (size_t)(G + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cc_destroy(c);
+        return fail(e == cudaErrorMemoryAllocation ? CC_ERR_OOM : CC_ERR_CUDA, "cc_create_segmented: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return CC_OK;
+}
+
+namespace {
+
+// Table layout in the staging and device buffers (fixed by the capacities,
+// so a captured graph keeps valid pointers): [nactive, pad x3][ops][op_begin
+// G+1][order G].
+struct TableLayout {
+    size_t ops, op_begin, order, bytes;
+};
+
+TableLayout table_layout(int64_t cap_ops, int32_t G) {
+    TableLayout L;
+    L.ops = 16;
+    L.op_begin = L.ops + sizeof(cc::SegOp) * (size_t)cap_ops;
+    L.order = L.op_begin + sizeof(int) * (size_t)(G + 1);
+    L.bytes = (L.order + sizeof(int) * (size_t)G + 255) / 256 * 256;
+    return L;
+}
+
+cc_status ensure_tables(cc_ctx* c, int64_t nops) {
+    if (!c->seg_off) {  // a plain handle is one graph
+        c->seg_off_h = {0, c->n};
+        cudaError_t e = cudaMalloc(&c->seg_off, sizeof(int64_t) * 2);
+        if (e == cudaSuccess) e = cudaMemcpy(c->seg_off, c->seg_off_h.data(), sizeof(int64_t) * 2, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "cc_submit: segment offsets");
+    }
+    if (!c->staging_free) {
+        cudaError_t e = cudaEventCreateWithFlags(&c->staging_free, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "cc_submit: event");
+    }
+    if (nops <= c->cap_ops) return CC_OK;
+    int64_t cap = c->cap_ops ? c->cap_ops : 1024;
+    while (cap < nops) cap *= 2;
+    if (c->staging_pending) {
+        cudaEventSynchronize(c->staging_free);
+        c->staging_pending = false;
+    }
+    const TableLayout L = table_layout(cap, c->G);
+    void* staging = nullptr;
+    void* tables = nullptr;
+    cudaError_t e = cudaMallocHost(&staging, L.bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&tables, L.bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (staging) cudaFreeHost(staging);
+        return fail(CC_ERR_OOM, "cc_submit: table buffers of %zu bytes", L.bytes);
+    }
+    cudaStreamSynchronize(c->stream);  // the old tables may still be read by a running submit
+    if (c->staging) cudaFreeHost(c->staging);
+    cudaFree(c->tables);
+    c->staging = staging;
+    c->tables = tables;
+    c->cap_ops = cap;
+    c->table_bytes = L.bytes;
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    return CC_OK;
+}
+
+cc::SegLaunch seg_cfg(const cc_ctx* c) {
+    cc::SegLaunch cfg;
+    cfg.block = (int)c->opt[CC_OPT_SEG_BLOCK];
+    cfg.ept = (int)c->opt[CC_OPT_SEG_EDGES_PER_THREAD];
+    cfg.smem_cap = (int)c->opt[CC_OPT_SEG_SMEM_CAP];
+    cfg.max_ctas = (int)c->opt[CC_OPT_SEG_MAX_CTAS];
+    return cfg;
+}
+
+}  // namespace
+
+cc_status cc_submit(cc_ctx* c, const cc_op* ops, int64_t nops) {
+    CC_CHECK_CTX(c);
+    if (nops < 0 || nops > INT32_MAX) return fail(CC_ERR_ARG, "cc_submit: nops out of range");
+    if (nops == 0) return CC_OK;
+    if (!ops) return fail(CC_ERR_ARG, "cc_submit: ops is null");
+    for (int64_t i = 0; i < nops; i++) {
+        const cc_op& o = ops[i];
+        if (o.graph < 0 || o.graph >= c->G) return fail(CC_ERR_ARG, "cc_submit: op %lld: graph %d out of [0, %d)", (long long)i, o.graph, c->G);
+        if (o.kind != CC_OP_UPDATE && o.kind != CC_OP_QUERY) return fail(CC_ERR_ARG, "cc_submit: op %lld: unknown kind %d", (long long)i, o.kind);
+        if (o.k < 0 || o.k > INT32_MAX) return fail(CC_ERR_ARG, "cc_submit: op %lld: k out of range", (long long)i);
+        if (o.k > 0 && (!o.data || reinterpret_cast<uintptr_t>(o.data) % 4)) return fail(CC_ERR_ARG, "cc_submit: op %lld: data null or not 4-byte aligned", (long long)i);
+        if (o.k > 0 && o.kind == CC_OP_QUERY && !o.out) return fail(CC_ERR_ARG, "cc_submit: op %lld: out is null", (long long)i);
+    }
+    CC_DEVICE(c);
+    cc_status st = ensure_tables(c, nops);
+    if (st != CC_OK) return st;
+    if (c->staging_pending) {  // the previous submit's copy must be done before refilling
+        cudaError_t e = cudaEventSynchronize(c->staging_free);
+        if (e != cudaSuccess) return cuda_fail(e, "cc_submit: wait for staging");
+        c->staging_pending = false;
+    }
+    // bucket the operations by graph, keeping their order within a graph
+    const int32_t G = c->G;
+    const TableLayout L = table_layout(c->cap_ops, G);
+    char* base = static_cast<char*>(c->staging);
+    cc::SegOp* sops = reinterpret_cast<cc::SegOp*>(base + L.ops);
+    int* op_begin = reinterpret_cast<int*>(base + L.op_begin);
+    int* order = reinterpret_cast<int*>(base + L.order);
+    c->bucket_count.assign((size_t)G + 1, 0);
+    c->work_h.assign((size_t)G, 0);
+    for (int64_t i = 0; i < nops; i++) {
+        c->bucket_count[ops[i].graph + 1]++;
+        c->work_h[ops[i].graph] += ops[i].k;
+    }
+    op_begin[0] = 0;
+    for (int32_t g = 0; g < G; g++) op_begin[g + 1] = op_begin[g] + c->bucket_count[g + 1];
+    c->op_begin_h.assign(op_begin, op_begin + G + 1);
+    for (int64_t i = 0; i < nops; i++) {
+        const cc_op& o = ops[i];
+        cc::SegOp& d = sops[c->op_begin_h[o.graph]++];
+        d.data = o.data;
+        d.out = o.out;
+        d.k = o.k;
+        d.kind = o.kind;
+        d.pad = 0;
+    }
+    // graphs with work, largest first (a graph's cost grows with its ops and its size)
+    c->order_h.clear();
+    for (int32_t g = 0; g < G; g++)
+        if (c->bucket_count[g + 1]) {
+            c->work_h[g] += c->seg_off_h[g + 1] - c->seg_off_h[g];
+            c->order_h.push_back(g);
+        }
+    std::stable_sort(c->order_h.begin(), c->order_h.end(),
+                     [&](int a, int b) { return c->work_h[a] > c->work_h[b]; });
+    memcpy(order, c->order_h.data(), sizeof(int) * c->order_h.size());
+    reinterpret_cast<int*>(base)[0] = (int)c->order_h.size();
+
+    cc::SegLaunch cfg = seg_cfg(c);
+    char* dbase = static_cast<char*>(c->tables);
+    cc::SegTables t;
+    t.ops = reinterpret_cast<const cc::SegOp*>(dbase + L.ops);
+    t.op_begin = reinterpret_cast<const int*>(dbase + L.op_begin);
+    t.order = reinterpret_cast<const int*>(dbase + L.order);
+    t.nactive = reinterpret_cast<const int*>(dbase);
+    const int64_t key[5] = {cfg.block, cfg.ept, cfg.smem_cap, cfg.max_ctas, c->cap_ops};
+    const bool use_graph = c->opt[CC_OPT_SEG_GRAPH] != 0;
+    st = run(c, CC_K_SEGMENTED, "submit", [&]() -> cudaError_t {
+        cudaError_t e;
+        if (use_graph) {
+            if (!c->graph_exec || memcmp(key, c->graph_key, sizeof key) != 0) {
+                if (c->graph_exec) {
+                    cudaGraphExecDestroy(c->graph_exec);
+                    c->graph_exec = nullptr;
+                }
+                e = cc::prepare_segmented(cfg);
+                if (e != cudaSuccess) return e;
+                if (!c->capture_stream) {
+                    e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
+                    if (e != cudaSuccess) return e;
+                }
+                cudaGraph_t graph = nullptr;
+                e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
+                if (e != cudaSuccess) return e;
+                cudaError_t e1 = cudaMemcpyAsync(c->tables, c->staging, c->table_bytes, cudaMemcpyHostToDevice, c->capture_stream);
+                if (e1 == cudaSuccess) e1 = cudaMemsetAsync(&c->ds->queue, 0, sizeof(unsigned), c->capture_stream);
+                if (e1 == cudaSuccess) e1 = cc::launch_segmented(c->parent, c->seg_off, t, &c->ds->queue, c->ds, cfg, c->capture_stream);
+                e = cudaStreamEndCapture(c->capture_stream, &graph);
+                if (e1 != cudaSuccess) e = e1;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                if (e != cudaSuccess) {
+                    c->graph_exec = nullptr;
+                    return e;
+                }
+                memcpy(c->graph_key, key, sizeof key);
+            }
+            e = cudaGraphLaunch(c->graph_exec, c->stream);
+        } else {
+            e = cc::prepare_segmented(cfg);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->tables, c->staging, L.order + sizeof(int) * c->order_h.size(), cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(&c->ds->queue, 0, sizeof(unsigned), c->stream);
+            if (e == cudaSuccess) e = cc::launch_segmented(c->parent, c->seg_off, t, &c->ds->queue, c->ds, cfg, c->stream);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(c->staging_free, c->stream);
+        return e;
+    });
+    if (st == CC_OK) c->staging_pending = true;
+    c->flat = false;
+    return st;
+}
+
 cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
     CC_CHECK_CTX(c);
     switch (option) {
@@ -377,6 +629,47 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
         case CC_OPT_PROFILE:
             if (value != 0 && value != 1) return fail(CC_ERR_ARG, "option %d takes 0 or 1", option);
             break;
+        case CC_OPT_SEG_BLOCK:
+            if (value < 64 || value > 1024 || value % 32) return fail(CC_ERR_ARG, "seg block %lld: need 64..1024, multiple of 32", (long long)value);
+            break;
+        case CC_OPT_SEG_EDGES_PER_THREAD:
+            if (value != 1 && value != 2 && value != 4) return fail(CC_ERR_ARG, "seg edges per thread %lld: need 1, 2 or 4", (long long)value);
+            break;
+        case CC_OPT_SEG_SMEM_CAP:
+            if (value < 0 || value > 65536) return fail(CC_ERR_ARG, "seg smem cap %lld: need 0..65536", (long long)value);
+            break;
+        case CC_OPT_SEG_GRAPH:
+            if (value != 0 && value != 1) return fail(CC_ERR_ARG, "option %d takes 0 or 1", option);
+            break;
+        case CC_OPT_SEG_MAX_CTAS:
+            if (value < 0 || value > (1 << 20)) return fail(CC_ERR_ARG, "seg max ctas %lld out of range", (long long)value);
+            break;
+        case CC_OPT_UPDATE_VARIANT:
+            if (value < 0 || value > 2) return fail(CC_ERR_ARG, "update variant %lld: need 0, 1 or 2", (long long)value);
+            break;
+        case CC_OPT_L2_PERSIST: {
+            if (value != 0 && value != 1) return fail(CC_ERR_ARG, "option %d takes 0 or 1", option);
+            c->window = cudaAccessPolicyWindow{};
+            if (value) {
+                DeviceScope scope(c->device);
+                int max_persist = 0, max_window = 0;
+                cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, c->device);
+                cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, c->device);
+                if (max_persist <= 0 || max_window <= 0)
+                    return fail(CC_ERR_UNSUPPORTED, "no persisting L2 on this device");
+                const size_t bytes = (size_t)c->n * sizeof(int);
+                const size_t limit = bytes < (size_t)max_persist ? bytes : (size_t)max_persist;
+                cudaError_t e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, limit);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSetLimit(persisting L2)");
+                c->window.base_ptr = c->parent;
+                c->window.num_bytes = bytes < (size_t)max_window ? bytes : (size_t)max_window;
+                c->window.hitRatio = (float)((double)limit / (double)c->window.num_bytes);
+                if (c->window.hitRatio > 1.f) c->window.hitRatio = 1.f;
+                c->window.hitProp = cudaAccessPropertyPersisting;
+                c->window.missProp = cudaAccessPropertyStreaming;
+            }
+            break;
+        }
         default:
             return fail(CC_ERR_ARG, "unknown option %d", option);
     }

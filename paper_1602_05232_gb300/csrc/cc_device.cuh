@@ -22,6 +22,12 @@ __device__ __forceinline__ void flag(DevState* ds, unsigned bit) { atomicOr(&ds-
 
 __device__ __forceinline__ bool in_range(int x, int n) { return (unsigned)x < (unsigned)n; }
 
+// Alignment class of a pair array: 2 = 16-byte, 1 = 8-byte, 0 = 4-byte.
+__device__ __forceinline__ int pair_vec_dev(const void* p) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    return (a % 16 == 0) ? 2 : (a % 8 == 0) ? 1 : 0;
+}
+
 // Root of x's tree, given p = parent[x] already read and p != x. Walks with
 // path halving: each visited node is repointed at its grandparent, which
 // roughly halves the path for later walks (the Section 5.1 idea of making
@@ -65,6 +71,45 @@ __device__ __forceinline__ int hook(int* parent, int ru, int rv, DevState* ds) {
         if (hi == ru) ru = r; else rv = r;
     }
     return 0;
+}
+
+// Walk W chains to their roots in lockstep with path splitting. Chain c is at
+// node x[c] whose parent p[c] has been read; it is finished when p[c] >= x[c]
+// (p == x: x is the root). Each round reads the grandparent of every
+// unfinished chain -- independent loads, all in flight together -- then
+// repoints the node at its grandparent and moves up one level. On exit x[c]
+// is the root of chain c (or, with a broken invariant, where it stopped).
+template <int W>
+__device__ __forceinline__ void walk_split(int* parent, int (&x)[W], int (&p)[W], DevState* ds) {
+    while (true) {
+        int gp[W];
+        bool any = false;
+#pragma unroll
+        for (int c = 0; c < W; c++) {
+            gp[c] = p[c];
+            if (p[c] < x[c]) {
+                gp[c] = parent[p[c]];
+                any = true;
+            }
+        }
+        if (!any) break;
+#pragma unroll
+        for (int c = 0; c < W; c++) {
+            if (p[c] < x[c]) {
+                if (gp[c] == p[c]) {
+                    x[c] = p[c];          // p is the root
+                } else if (gp[c] > p[c]) {
+                    flag(ds, ST_CORRUPT);
+                    x[c] = p[c];
+                    p[c] = x[c];
+                } else {
+                    parent[x[c]] = gp[c];  // splitting: skip a level
+                    x[c] = p[c];
+                    p[c] = gp[c];
+                }
+            }
+        }
+    }
 }
 
 // Read-only walk to the root from x with p = parent[x] already read.

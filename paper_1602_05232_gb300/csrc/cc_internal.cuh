@@ -20,11 +20,14 @@ struct DevState {
     unsigned labels_bad;        // set by the label validator
     unsigned long long unions;  // successful hooks since create / reset
     unsigned long long roots;   // roots counted by the label validator
+    unsigned queue;             // work-queue counter of the batched form
+    unsigned pad;
 };
 
 struct Launch {
-    int block;  // threads per block, multiple of 32
-    int ept;    // edges (pairs) per thread: 1, 2 or 4
+    int block;        // threads per block, multiple of 32
+    int ept;          // edges (pairs) per thread: 1, 2 or 4
+    int variant = 0;  // update kernel: 0 per-edge walks, 1 lockstep walks, 2 persistent + prefetch
 };
 
 // Alignment class of a pair array: 2 = 16-byte, 1 = 8-byte, 0 = 4-byte.
@@ -49,6 +52,42 @@ cudaError_t launch_compress_all(int* parent, int64_t n, int* out, DevState* ds, 
 
 cudaError_t launch_compress_touched(int* parent, int n, const int* edges, int64_t k,
                                     DevState* ds, Launch cfg, cudaStream_t s);
+
+// ---- batched form (segmented forests, one persistent kernel) ----
+
+// One bulk operation of the batched form, as the kernel reads it.
+struct SegOp {
+    const int* data;  // 2k local ids
+    uint8_t* out;     // k answers (queries)
+    int64_t k;
+    int32_t kind;     // CC_OP_UPDATE / CC_OP_QUERY
+    int32_t pad;
+};
+
+// Per-submit tables in device memory: ops grouped by graph (list order kept
+// within a graph), op_begin[G+1] delimiting each graph's ops, and the order in
+// which CTAs claim the *nactive graphs that have work.
+struct SegTables {
+    const SegOp* ops;
+    const int* op_begin;
+    const int* order;
+    const int* nactive;
+};
+
+struct SegLaunch {
+    int block;     // threads per CTA
+    int ept;       // edges (pairs) per thread per step: 1, 2 or 4
+    int smem_cap;  // graphs of at most this many vertices run in shared memory (<= 65536)
+    int max_ctas;  // cap on the persistent grid (0 = one wave of resident CTAs)
+    int grid = 0;  // set by prepare_segmented
+};
+
+// Sets the kernel's shared-memory attribute and the persistent grid size.
+// Call before launching or capturing.
+cudaError_t prepare_segmented(SegLaunch& cfg);
+
+cudaError_t launch_segmented(int* parent, const int64_t* seg_off, const SegTables& t,
+                             unsigned* queue, DevState* ds, const SegLaunch& cfg, cudaStream_t s);
 
 // Checks 0 <= lab[v] <= v and lab[lab[v]] == lab[v]; counts roots.
 cudaError_t launch_validate_labels(const int* lab, int64_t n, DevState* ds, int block,

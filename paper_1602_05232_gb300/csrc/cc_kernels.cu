@@ -36,38 +36,35 @@ cudaError_t launch_reset(int* parent, int64_t n, int block, cudaStream_t s) {
 
 // ------------------------------------------------------------ Bulk-Update
 
-// One fused pass of Algorithm 2 over E edges per thread. The first parent
-// reads of both endpoints of all E edges are issued together; equal parents
-// mean the edge joins a tree to itself and is dropped at once (the common
-// case once trees are flat). Otherwise both roots are found with path
-// halving and hooked.
-template <int E>
-__global__ void __launch_bounds__(1024)
-k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
-         DevState* __restrict__ ds) {
-    const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
+// One fused pass of Algorithm 2 over E edges: the first parent reads of both
+// endpoints of all E edges are issued together; equal parents mean the edge
+// joins a tree to itself and is dropped at once (the common case once trees
+// are flat, and the self-loop filter of Algorithm 2). The other endpoints are
+// walked to their roots -- VARIANT 0 one edge at a time with path halving,
+// VARIANTs 1 and 2 all 2E walks in lockstep with path splitting -- and the
+// roots are hooked. Returns the number of links made.
+template <int E, int VARIANT>
+__device__ __forceinline__ int update_edges(int* __restrict__ parent, int n,
+                                            const int (&u)[E], const int (&v)[E], int64_t e0,
+                                            int64_t k, DevState* __restrict__ ds) {
+    bool ok[E];
+    bool bad = false;
     int made = 0;
-    if (e0 < k) {
-        int u[E], v[E], pu[E], pv[E];
-        bool ok[E];
-        bool bad = false;
-        load_pairs<E>(edges, e0, k, vec, u, v);
 #pragma unroll
-        for (int i = 0; i < E; i++) {
-            ok[i] = e0 + i < k;
-            if (ok[i] && !(in_range(u[i], n) && in_range(v[i], n))) {
-                ok[i] = false;
-                bad = true;
-            }
-            pu[i] = 0;
-            pv[i] = 0;
+    for (int i = 0; i < E; i++) {
+        ok[i] = e0 + i < k;
+        if (ok[i] && !(in_range(u[i], n) && in_range(v[i], n))) {
+            ok[i] = false;
+            bad = true;
         }
+    }
+    if (bad) flag(ds, ST_RANGE);
+    if (VARIANT == 0) {
+        int pu[E], pv[E];
 #pragma unroll
         for (int i = 0; i < E; i++) {
-            if (ok[i]) {
-                pu[i] = parent[u[i]];
-                pv[i] = parent[v[i]];
-            }
+            pu[i] = ok[i] ? parent[u[i]] : 0;
+            pv[i] = ok[i] ? parent[v[i]] : 0;
         }
 #pragma unroll
         for (int i = 0; i < E; i++) {
@@ -76,22 +73,111 @@ k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t
             int rv = pv[i] == v[i] ? v[i] : find_from(parent, v[i], pv[i], ds);
             made += hook(parent, ru, rv, ds);
         }
-        if (bad) flag(ds, ST_RANGE);
+        return made;
+    }
+    // lockstep: chain c = 2i (u side) and 2i+1 (v side); finished when p >= x
+    int x[2 * E], p[2 * E];
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        x[2 * i] = ok[i] ? u[i] : 0;
+        x[2 * i + 1] = ok[i] ? v[i] : 0;
+    }
+#pragma unroll
+    for (int c = 0; c < 2 * E; c++) p[c] = ok[c / 2] ? parent[x[c]] : x[c];
+    bool live[E];
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        live[i] = ok[i] && p[2 * i] != p[2 * i + 1];
+        if (!live[i]) {  // nothing to walk for this edge
+            p[2 * i] = x[2 * i];
+            p[2 * i + 1] = x[2 * i + 1];
+        }
+    }
+    walk_split<2 * E>(parent, x, p, ds);
+#pragma unroll
+    for (int i = 0; i < E; i++)
+        if (live[i]) made += hook(parent, x[2 * i], x[2 * i + 1], ds);
+    return made;
+}
+
+template <int E, int VARIANT>
+__global__ void __launch_bounds__(1024)
+k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
+         DevState* __restrict__ ds) {
+    int made = 0;
+    int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
+    if (VARIANT < 2) {
+        if (e0 < k) {
+            int u[E], v[E];
+            load_pairs<E>(edges, e0, k, vec, u, v);
+            made = update_edges<E, VARIANT>(parent, n, u, v, e0, k, ds);
+        }
+    } else {
+        // persistent grid: loop over chunks, loading the next chunk's edges
+        // before walking the current one so their latency overlaps
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x * E;
+        int u[E], v[E];
+        if (e0 < k) load_pairs<E>(edges, e0, k, vec, u, v);
+        while (e0 < k) {
+            const int64_t nx = e0 + stride;
+            int nu[E] = {}, nv[E] = {};
+            if (nx < k) load_pairs<E>(edges, nx, k, vec, nu, nv);
+            made += update_edges<E, 1>(parent, n, u, v, e0, k, ds);
+#pragma unroll
+            for (int i = 0; i < E; i++) {
+                u[i] = nu[i];
+                v[i] = nv[i];
+            }
+            e0 = nx;
+        }
     }
     made = __reduce_add_sync(0xffffffffu, made);
     if ((threadIdx.x & 31) == 0 && made) atomicAdd(&ds->unions, (unsigned long long)made);
+}
+
+template <int E, int VARIANT>
+static int resident_blocks(int block) {
+    static int cached[33] = {};
+    int& c = cached[block / 32];
+    if (!c) {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update<E, VARIANT>, block, 0);
+        c = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    }
+    return c;
+}
+
+template <int E, int VARIANT>
+static void update_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
+                        int block, cudaStream_t s) {
+    int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
+    if (VARIANT == 2) {
+        const int64_t cap = resident_blocks<E, VARIANT>(block);
+        if (g > cap) g = cap;
+    }
+    k_update<E, VARIANT><<<(unsigned)g, block, 0, s>>>(parent, n, edges, k, vec, ds);
 }
 
 cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevState* ds,
                           Launch cfg, cudaStream_t s) {
     if (k <= 0) return cudaSuccess;
     const int vec = pair_vec(edges);
-    const unsigned g = blocks_for(k, (int64_t)cfg.ept * cfg.block);
-    switch (cfg.ept) {
-        case 1: k_update<1><<<g, cfg.block, 0, s>>>(parent, n, edges, k, vec, ds); break;
-        case 2: k_update<2><<<g, cfg.block, 0, s>>>(parent, n, edges, k, vec, ds); break;
-        default: k_update<4><<<g, cfg.block, 0, s>>>(parent, n, edges, k, vec, ds); break;
+#define CC_UPD(E, V) update_inst<E, V>(edges, k, vec, parent, n, ds, cfg.block, s)
+    switch (cfg.variant * 8 + cfg.ept) {
+        case 1: CC_UPD(1, 0); break;
+        case 2: CC_UPD(2, 0); break;
+        case 4: CC_UPD(4, 0); break;
+        case 9: CC_UPD(1, 1); break;
+        case 10: CC_UPD(2, 1); break;
+        case 12: CC_UPD(4, 1); break;
+        case 17: CC_UPD(1, 2); break;
+        case 18: CC_UPD(2, 2); break;
+        case 20: CC_UPD(4, 2); break;
+        default: return cudaErrorInvalidValue;
     }
+#undef CC_UPD
     return cudaGetLastError();
 }
 

@@ -1,0 +1,166 @@
+"""Batched form (one persistent kernel over many graphs, cc_submit) against a
+per-graph CPU oracle: every answer of every query minibatch and the final
+minimum-id labels of every graph, bit-exact."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1602_05232_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1602_05232_gb300 import _build, cc as ccmod
+    _build.build_cc()
+    ccmod.load()
+    return ccmod
+
+
+def build_ops(cc, w, interleave_seed=None):
+    """Device copies of every graph's edges and pairs, the op table in stream
+    order (optionally interleaved across graphs, order kept per graph), and
+    the answer buffers."""
+    d_e, d_q, outs, per_graph = [], [], [], []
+    for g in range(w.G):
+        d_e.append(torch.from_numpy(w.edges(g)).cuda())
+        d_q.append(torch.from_numpy(w.queries(g)).cuda())
+        per_graph.append(w.ops(g))
+    out = torch.zeros(sum(w.m(g) for g in range(w.G)), dtype=torch.uint8, device="cuda")
+    qbase = np.concatenate([[0], np.cumsum([w.m(g) for g in range(w.G)])])
+    seq = [(g, j) for g in range(w.G) for j in range(len(per_graph[g]))]
+    if interleave_seed is not None:
+        # a random interleaving of the graphs' op lists that keeps each graph's order
+        rng = np.random.default_rng(interleave_seed)
+        pool = [g for g in range(w.G) for _ in per_graph[g]]
+        heads = [0] * w.G
+        seq = []
+        for idx in rng.permutation(len(pool)):
+            g = pool[idx]
+            seq.append((g, heads[g]))
+            heads[g] += 1
+    ops = np.zeros(len(seq), dtype=cc.OP_DTYPE)
+    for i, (g, j) in enumerate(seq):
+        kind, off, size = per_graph[g][j]
+        src = d_e[g] if kind == 0 else d_q[g]
+        ops[i]["graph"] = g
+        ops[i]["kind"] = kind
+        ops[i]["data"] = src.data_ptr() + 8 * off
+        ops[i]["k"] = size
+        ops[i]["out"] = out.data_ptr() + int(qbase[g]) + off if kind == 1 else 0
+    return ops, out, qbase, (d_e, d_q)
+
+
+def oracle_answers(w, qbase):
+    want = np.zeros(int(qbase[-1]), dtype=np.uint8)
+    labels = []
+    for g in range(w.G):
+        uf = oracle.OracleUF(int(w.n[g]))
+        e, q = w.edges(g), w.queries(g)
+        for kind, off, size in w.ops(g):
+            if kind == 0:
+                uf.bulk_update(e[off:off + size])
+            else:
+                want[int(qbase[g]) + off:int(qbase[g]) + off + size] = uf.bulk_query(q[off:off + size])
+        labels.append(uf.labels())
+    return want, labels
+
+
+def check(cc, w, options, interleave_seed=None):
+    f = cc.Forest.segmented(w.n, **options)
+    ops, out, qbase, keep = build_ops(cc, w, interleave_seed)
+    f.submit(ops)
+    got = out.cpu().numpy()
+    f.sync()
+    want, labels = oracle_answers(w, qbase)
+    assert np.array_equal(got, want), f"{int((got != want).sum())} answers differ"
+    lab = f.labels().cpu().numpy()
+    for g in range(w.G):
+        o0, o1 = int(f.offsets[g]), int(f.offsets[g + 1])
+        assert np.array_equal(lab[o0:o1] - o0, labels[g]), f"labels of graph {g}"
+    assert f.components() == sum(len(np.unique(l)) for l in labels)
+    return f
+
+
+@pytest.mark.parametrize("opts", [
+    {},
+    {"seg_graph": 0},
+    {"seg_block": 256, "seg_edges_per_thread": 2},
+    {"seg_block": 1024, "seg_edges_per_thread": 4},
+    {"seg_smem_cap": 1000},          # larger graphs in global memory
+    {"seg_smem_cap": 0},             # every graph in global memory
+    {"seg_max_ctas": 7},             # few CTAs: each claims many graphs
+])
+def test_segmented_small(cc, opts):
+    w = I.segmented_workload(G=48, seed=3, nlo=4, nhi=12, blo=2, bhi=9)
+    check(cc, w, opts)
+
+
+def test_segmented_interleaved_ops(cc):
+    w = I.segmented_workload(G=40, seed=4, nlo=5, nhi=11, blo=3, bhi=8)
+    check(cc, w, {}, interleave_seed=1)
+
+
+def test_segmented_full_size_and_replay(cc):
+    # 1024 graphs, n log-uniform in [2^8, 2^16), m = 4n, minibatches log-uniform
+    # in [2^6, 2^14): the whole workload in one submit, then replayed on a reset
+    # forest through the captured graph and checked again
+    w = I.segmented_workload()
+    f = check(cc, w, {})
+    f.reset()
+    ops, out, qbase, keep = build_ops(cc, w)
+    f.submit(ops)
+    got = out.cpu().numpy()
+    want, _ = oracle_answers(w, qbase)
+    assert np.array_equal(got, want)
+    assert f.kernel_stats()["segmented"] == 2
+
+
+def test_submit_errors_and_plain_ids(cc):
+    w = I.segmented_workload(G=4, seed=5, nlo=4, nhi=6, blo=2, bhi=4)
+    f = cc.Forest.segmented(w.n)
+    e = torch.zeros((3, 2), dtype=torch.int32, device="cuda")
+    with pytest.raises(cc.CCError) as ex:
+        f.submit([(4, cc.OP_UPDATE, e, None)])
+    assert ex.value.status == cc.CC_ERR_ARG
+    with pytest.raises(cc.CCError):
+        f.submit([(0, cc.OP_QUERY, e, None)])
+    # out-of-range local ids are skipped and reported
+    bad = torch.tensor([[0, int(w.n[0])], [0, 1]], dtype=torch.int32, device="cuda")
+    f.submit([(0, cc.OP_UPDATE, bad, None)])
+    with pytest.raises(cc.CCError) as ex:
+        f.sync()
+    assert ex.value.status == cc.CC_ERR_RANGE
+    # the forest of a segmented handle changes only through cc_submit
+    o1 = int(f.offsets[1])
+    with pytest.raises(cc.CCError) as ex:
+        f.bulk_update(torch.tensor([[0, o1]], dtype=torch.int32, device="cuda"))
+    assert ex.value.status == cc.CC_ERR_UNSUPPORTED
+    # Bulk-Query takes global ids on a segmented handle
+    f.submit([(1, cc.OP_UPDATE, torch.tensor([[0, 1]], dtype=torch.int32, device="cuda"), None)])
+    q = torch.tensor([[0, 1], [o1, o1 + 1], [0, o1]], dtype=torch.int32, device="cuda")
+    assert f.bulk_query(q).cpu().tolist() == [1, 1, 0]
+
+
+def test_submit_on_plain_handle(cc):
+    s = I.uniform_stream(n=3000, m=6000, batch=1000, q=500, seed=6)
+    f = cc.Forest(s.n)
+    ref = oracle.OracleUF(s.n)
+    keep, ops = [], []
+    outs = []
+    for e, q in s:
+        de, dq = torch.from_numpy(e).cuda(), torch.from_numpy(q).cuda()
+        o = torch.zeros(len(q), dtype=torch.uint8, device="cuda")
+        keep += [de, dq]
+        outs.append(o)
+        ops += [(0, cc.OP_UPDATE, de, None), (0, cc.OP_QUERY, dq, o)]
+    f.submit(ops)
+    for (e, q), o in zip(s, outs):
+        ref.bulk_update(e)
+        assert np.array_equal(o.cpu().numpy(), ref.bulk_query(q))

@@ -26,6 +26,11 @@ OPTION_SETS = {
     "no_compress_halving_query": {"compress_every": 0, "query_halving": 1},
     "touched_compress": {"compress_scope": 1},
     "compress_every3": {"compress_every": 3},
+    "lockstep": {"update_variant": 1},
+    "lockstep_ept4_nocompress": {"update_variant": 1, "edges_per_thread": 4, "compress_every": 0},
+    "persistent_ept4": {"update_variant": 2, "edges_per_thread": 4},
+    "persistent_ept1_b1024": {"update_variant": 2, "edges_per_thread": 1, "block": 1024},
+    "l2_persist": {"l2_persist": 1, "update_variant": 2, "edges_per_thread": 2},
 }
 
 
@@ -80,13 +85,15 @@ def test_uniform_small_every_batch(cc, opts):
                check_invariants=(opts == "default"))
 
 
-@pytest.mark.parametrize("opts", ["default", "ept1_b64", "no_compress", "touched_compress"])
+@pytest.mark.parametrize("opts", ["default", "ept1_b64", "no_compress", "touched_compress",
+                                  "lockstep_ept4_nocompress", "persistent_ept4"])
 def test_rmat_small(cc, opts):
     s = I.rmat_stream(scale=16, m=1 << 20, batch=(1 << 16) + 3, q=(1 << 16) - 5, seed=1)
     run_stream(cc, s, OPTION_SETS[opts], label_every=4, check_invariants=True)
 
 
-@pytest.mark.parametrize("opts", ["default", "no_compress", "ept4_b1024", "compress_every3"])
+@pytest.mark.parametrize("opts", ["default", "no_compress", "ept4_b1024", "compress_every3",
+                                  "lockstep", "persistent_ept1_b1024"])
 def test_grid_small(cc, opts):
     s = I.grid_stream(512, 512, batch=(1 << 14) + 1, q=1 << 14, seed=2)
     ref = run_stream(cc, s, OPTION_SETS[opts], label_every=8, check_invariants=True)
