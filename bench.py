@@ -51,6 +51,8 @@ LAUNCH_OPTIONS = {
              "compress_scope": 0},
     "segmented": {"seg_block": 512, "seg_edges_per_thread": 1, "seg_smem_cap": 65536,
                   "seg_graph": 1},
+    "serving": {"block": 256, "edges_per_thread": 4, "update_variant": 2, "compress_every": 0,
+                "compress_scope": 0},
 }
 
 
@@ -78,6 +80,8 @@ WORKLOAD_TEXT = {
             "Bulk-Updates of 2^22, each followed by a Bulk-Query of 2^22 uniform pairs",
     "segmented": "1024 graphs, n log-uniform in [2^8,2^16), m=4n uniform edges, minibatches "
                  "log-uniform in [2^6,2^14), each followed by a Bulk-Query of the same size",
+    "serving": "request loop on one R-MAT n=2^26 stream (2^30 edges): Poisson arrivals, "
+               "3:1 updates (log-uniform [2^8,2^20] edges) to queries (log-uniform [2^8,2^18] pairs)",
 }
 
 
@@ -306,6 +310,111 @@ def run_segmented(args, rank: int, world: int, local_rank: int, dist) -> dict:
                        "launches_per_pass": len(seq), "what": "one cc_bulk_update / "
                        "cc_bulk_query launch per minibatch on a plain handle, global ids"},
         "speedup_vs_plain": round(ms_plain / (ms / args.steps), 2),
+        "clocks": clk.summary(),
+    }
+
+
+# ------------------------------------------------------------ serving form
+
+def run_serving(args, rank: int, world: int, local_rank: int, dist) -> dict:
+    """Served form: the whole request trace through cc_server (continuous
+    batching). Saturation: every request enqueued at once, edges/s from first
+    enqueue to drain. Then the trace replayed at 0.5 / 0.8 / 0.95 of that
+    capacity with Poisson arrivals for p50/p99 latency. Plain form: the same
+    requests one at a time (copy in, one launch, copy out, wait)."""
+    import torch
+    from paper_1602_05232_gb300 import cc, inputs as I
+
+    torch.cuda.set_device(local_rank)
+    scale = args.serve_scale
+    m = 1 << (scale + 4)
+    s = I.rmat_stream(scale=scale, m=m, batch=m, q=1, seed=rank)
+    h_edges = torch.empty((m, 2), dtype=torch.int32, pin_memory=True)
+    s.all_edges(out=h_edges.numpy())
+    nominal = 1000.0
+    reqs = I.request_trace(m, rate_hz=nominal, seed=rank)
+    qtot = sum(r.size for r in reqs if r.kind == 1)
+    h_pairs = torch.empty((qtot, 2), dtype=torch.int32, pin_memory=True)
+    I.uniform_pairs(s.n, qtot, rank, I.TAG_QUERIES, 0, out=h_pairs.numpy())
+    h_out = torch.empty(qtot, dtype=torch.uint8, pin_memory=True)
+    views = []
+    for r in reqs:
+        if r.kind == 0:
+            views.append((0, h_edges[r.offset:r.offset + r.size], None))
+        else:
+            views.append((1, h_pairs[r.offset:r.offset + r.size], h_out[r.offset:r.offset + r.size]))
+    opts = launch_options("serving")
+
+    def serve(rate: float | None):
+        f = cc.Forest(s.n, **opts)
+        with cc.Server(f) as srv:
+            t0 = time.perf_counter()
+            for r, (kind, d, o) in zip(reqs, views):
+                if rate is not None:
+                    due = r.t * nominal / rate
+                    while time.perf_counter() - t0 < due:
+                        pass
+                srv.enqueue(kind, d, o)
+            srv.drain()
+            dt = time.perf_counter() - t0
+            lat = srv.latencies()
+            st = srv.stats()
+        labels = f.labels()
+        f.close()
+        return dt, lat, st, labels
+
+    serve(None)                                  # warm-up
+    dist_barrier(dist)
+    with ClockSampler(local_rank) as clk:
+        dt_sat, lat_sat, st_sat, lab_served = serve(None)
+    dist_barrier(dist)
+    cap_edges = m / dt_sat
+    cap_rps = len(reqs) / dt_sat
+    loads = {}
+    for load_frac in (0.5, 0.8, 0.95):
+        rate = cap_rps * load_frac
+        dt, lat, st, _ = serve(rate)
+        loads[str(load_frac)] = {"offered_req_per_s": round(rate, 1),
+                                 "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+                                 "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+                                 "edges_per_s": round(m / dt, 1), "groups": st["groups"]}
+    # plain form: one request at a time through the plain API
+    f = cc.Forest(s.n, **opts)
+    dev = torch.device("cuda", local_rank)
+    kmax = max(r.size for r in reqs)
+    d_in = torch.empty((kmax, 2), dtype=torch.int32, device=dev)
+    d_o = torch.empty(kmax, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for kind, d, o in views:
+        k = d.shape[0]
+        d_in[:k].copy_(d, non_blocking=True)
+        if kind == 0:
+            f.bulk_update(d_in[:k])
+        else:
+            f.bulk_query(d_in[:k], out=d_o[:k])
+            o.copy_(d_o[:k], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    dt_plain = time.perf_counter() - t0
+    same = bool(torch.equal(f.labels(), lab_served))
+    f.close()
+    value = dist_sum(dist, cap_edges, dev)
+    return {
+        "metric": METRIC, "value": round(value, 1), "unit": "edges/s", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": round(1e3 * dt_sat, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "form": "served",
+        "config": {"workload": WORKLOAD_TEXT["serving"] if scale == 26 else
+                   f"serving trace on R-MAT scale {scale}", "n": s.n, "edges": m,
+                   "requests": len(reqs), "query_pairs": qtot, "options": opts},
+        "saturation": {"edges_per_s": round(cap_edges, 1), "req_per_s": round(cap_rps, 1),
+                       "p50_ms": round(1e3 * float(np.percentile(lat_sat, 50)), 3),
+                       "p99_ms": round(1e3 * float(np.percentile(lat_sat, 99)), 3),
+                       "groups": st_sat["groups"]},
+        "latency_at_load": loads,
+        "plain_form": {"edges_per_s": round(m / dt_plain, 1), "seconds": round(dt_plain, 3),
+                       "what": "each request alone: copy in, one launch, copy out, synchronise"},
+        "served_labels_equal_plain": same,
         "clocks": clk.summary(),
     }
 
@@ -592,6 +701,8 @@ def main(argv=None) -> int:
     ap.add_argument("--ref-fraction", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-scale", type=int, default=26,
+                    help="R-MAT scale of the serving trace (2^(scale+4) edges)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -602,6 +713,8 @@ def main(argv=None) -> int:
         dist = dist_init(world, "nccl")
         if args.workload == "segmented":
             out = run_segmented(args, rank, world, local_rank, dist)
+        elif args.workload == "serving":
+            out = run_serving(args, rank, world, local_rank, dist)
         else:
             out = run_gpu(args, rank, world, local_rank, dist)
         if dist is not None:

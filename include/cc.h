@@ -221,6 +221,76 @@ typedef struct {
  * enqueued; out-of-range local ids are reported by cc_sync (CC_ERR_RANGE). */
 cc_status cc_submit(cc_ctx* ctx, const cc_op* ops, int64_t nops);
 
+/* ------------------------------------------------------- serving form */
+
+/* A request loop over one forest. Requests are admitted in arrival order.
+ * Updates take the next stream edges; queries are vertex pairs whose answers
+ * must reflect exactly the updates that arrived before them (Section 1: each
+ * bulk operation completes before the next one starts).
+ *
+ * Continuous batching: a worker thread takes the requests that have arrived
+ * and cuts them into groups of consecutive same-kind requests:
+ *  - A group of updates runs as ONE Bulk-Update launch. This is exact: G_t is
+ *    the union of the edge sets, and union is commutative and associative.
+ *  - A group of queries runs as ONE Bulk-Query launch.
+ * The stages overlap on the device:
+ *  - Request data is copied from host memory into a device staging ring on a
+ *    copy stream while earlier groups compute.
+ *  - Query answers go back on a second copy stream.
+ *  - Groups compute in arrival order on one compute stream, so no query
+ *    overlaps a later update.
+ * A request is admitted when its footprint (8 bytes in + 1 byte out per
+ * pair) fits in the free part of the ring; otherwise it waits for earlier
+ * groups to finish. Latency runs from enqueue to the host callback that
+ * follows the group's last device operation. */
+typedef struct cc_server cc_server;
+
+typedef struct {
+    int64_t ring_pairs;       /* staging capacity in pairs (<= 0: 2^25, i.e. 288 MiB) */
+    int64_t max_group_pairs;  /* most pairs merged into one launch (<= 0: 2^22) */
+    int32_t merge;            /* 1: merge consecutive same-kind requests (default); 0: one launch per request */
+} cc_server_config;
+
+typedef struct {
+    int64_t requests, updates, queries;  /* enqueued so far */
+    int64_t completed;
+    int64_t groups;                      /* launches (groups) issued */
+    int64_t edges, pairs;                /* total update edges and query pairs enqueued */
+} cc_server_stats;
+
+/* Start a server on `ctx` (a handle from cc_create). The server binds the
+ * handle to its own compute stream until cc_server_destroy, and the caller
+ * must not use the handle meanwhile. cfg may be NULL (defaults). */
+cc_status cc_server_create(cc_ctx* ctx, const cc_server_config* cfg, cc_server** out);
+
+/* Enqueue one request; returns at once with a ticket (0, 1, 2, ... in arrival
+ * order). kind is CC_OP_UPDATE or CC_OP_QUERY. `data` is a HOST array of 2k
+ * int32 (pinned memory lets copies overlap), read before the request
+ * completes. `out` is a host array of k bytes (queries), written before
+ * completion. Both stay owned by the caller and must stay valid until then.
+ * Errors: CC_ERR_ARG if k exceeds the ring or an argument is bad;
+ * CC_ERR_CUDA if the worker has failed. */
+cc_status cc_server_enqueue(cc_server* s, int32_t kind, const int32_t* data, int64_t k,
+                            uint8_t* out, uint64_t* ticket);
+
+/* Block until request `ticket` completes; *latency_s (may be NULL) receives
+ * its enqueue-to-completion time in seconds. */
+cc_status cc_server_wait(cc_server* s, uint64_t ticket, double* latency_s);
+
+/* Block until every enqueued request has completed. */
+cc_status cc_server_drain(cc_server* s);
+
+cc_status cc_server_get_stats(cc_server* s, cc_server_stats* out);
+
+/* Latencies in seconds of requests 0 .. n-1 in ticket order (host array of n
+ * doubles; -1 for a request not yet complete); *written receives min(n,
+ * requests). */
+cc_status cc_server_latencies(cc_server* s, double* out, int64_t n, int64_t* written);
+
+/* Drain, stop the worker, free the server's memory and streams, and give the
+ * handle back (bound again to the stream it had before). */
+cc_status cc_server_destroy(cc_server* s);
+
 /* ----------------------------------------------------------- tunables */
 
 cc_status cc_set_option(cc_ctx* ctx, int32_t option, int64_t value);

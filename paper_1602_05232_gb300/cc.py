@@ -78,6 +78,13 @@ def load(path: str | Path | None = None) -> ctypes.CDLL:
         "cc_kernel_stats": [vp, u64p, vp],
         "cc_create_segmented": [i32, vp, ctypes.POINTER(ctypes.c_void_p)],
         "cc_submit": [vp, vp, i64],
+        "cc_server_create": [vp, vp, ctypes.POINTER(ctypes.c_void_p)],
+        "cc_server_enqueue": [vp, i32, vp, i64, vp, ctypes.POINTER(ctypes.c_uint64)],
+        "cc_server_wait": [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)],
+        "cc_server_drain": [vp],
+        "cc_server_get_stats": [vp, vp],
+        "cc_server_latencies": [vp, vp, i64, ctypes.POINTER(ctypes.c_int64)],
+        "cc_server_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -252,3 +259,80 @@ class Forest:
         if timing:
             return {k: (int(counts[i]), float(ms[i])) for i, k in enumerate(KERNELS)}
         return {k: int(counts[i]) for i, k in enumerate(KERNELS)}
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("ring_pairs", ctypes.c_int64), ("max_group_pairs", ctypes.c_int64),
+                ("merge", ctypes.c_int32)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in
+                ("requests", "updates", "queries", "completed", "groups", "edges", "pairs")]
+
+
+class Server:
+    """Continuous-batching request loop over a Forest (cc_server_*).
+
+    ``enqueue`` takes HOST tensors (pinned for overlapped copies): int32 (k, 2)
+    data and, for queries, a uint8 (k,) output that is filled before the
+    request completes. The Forest must not be used directly while the server
+    runs."""
+
+    def __init__(self, forest: Forest, ring_pairs: int = 0, max_group_pairs: int = 0,
+                 merge: bool = True):
+        self._L = forest._L
+        self.forest = forest
+        cfg = _ServerConfig(ring_pairs, max_group_pairs, 1 if merge else 0)
+        h = ctypes.c_void_p()
+        check(self._L.cc_server_create(forest._h, ctypes.byref(cfg), ctypes.byref(h)), self._L)
+        self._h = h
+        self._keep: dict[int, tuple] = {}
+
+    def enqueue(self, kind: int, data: torch.Tensor, out: torch.Tensor | None = None) -> int:
+        if data.is_cuda or data.dtype != torch.int32 or not data.is_contiguous():
+            raise TypeError("data: expected a contiguous host int32 tensor")
+        k = data.numel() // 2
+        optr = 0
+        if kind == OP_QUERY:
+            if out is None or out.is_cuda or out.dtype != torch.uint8 or out.numel() < k:
+                raise TypeError("out: expected a host uint8 tensor of k elements")
+            optr = out.data_ptr()
+        t = ctypes.c_uint64()
+        check(self._L.cc_server_enqueue(self._h, kind, data.data_ptr(), k, optr, ctypes.byref(t)),
+              self._L)
+        self._keep[t.value] = (data, out)   # keep the buffers alive until drained
+        return t.value
+
+    def wait(self, ticket: int) -> float:
+        lat = ctypes.c_double()
+        check(self._L.cc_server_wait(self._h, ticket, ctypes.byref(lat)), self._L)
+        return lat.value
+
+    def drain(self) -> None:
+        check(self._L.cc_server_drain(self._h), self._L)
+        self._keep.clear()
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        check(self._L.cc_server_get_stats(self._h, ctypes.byref(st)), self._L)
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def latencies(self) -> np.ndarray:
+        n = self.stats()["requests"]
+        out = np.empty(n, dtype=np.float64)
+        w = ctypes.c_int64()
+        check(self._L.cc_server_latencies(self._h, out.ctypes.data, n, ctypes.byref(w)), self._L)
+        return out[:w.value]
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            check(self._L.cc_server_destroy(self._h), self._L)
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -164,6 +164,9 @@ cc_status do_compress(cc_ctx* c, int scope, const int32_t* edges, int64_t k) {
 namespace cc {
 // Lets the other translation units leave a message for cc_last_error_string().
 cc_status record_error(cc_status s, const char* msg) { return fail(s, "%s", msg); }
+cudaStream_t ctx_stream(const cc_ctx* c) { return c->stream; }
+int ctx_device(const cc_ctx* c) { return c->device; }
+int32_t ctx_graphs(const cc_ctx* c) { return c->G; }
 }  // namespace cc
 
 #define CC_CHECK_CTX(c)                                            \

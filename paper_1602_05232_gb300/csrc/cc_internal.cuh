@@ -36,6 +36,11 @@ int pair_vec(const void* p);
 // Sets the text returned by cc_last_error_string() and returns s.
 cc_status record_error(cc_status s, const char* msg);
 
+// The stream a handle is bound to, and its device.
+cudaStream_t ctx_stream(const cc_ctx* c);
+int ctx_device(const cc_ctx* c);
+int32_t ctx_graphs(const cc_ctx* c);
+
 cudaError_t launch_reset(int* parent, int64_t n, int block, cudaStream_t s);
 
 cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevState* ds,

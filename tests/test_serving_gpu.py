@@ -1,0 +1,155 @@
+"""Serving form (cc_server_*): requests enqueued as they arrive, merged and
+overlapped on the device, must give every query the same answers as running
+each request alone, in arrival order, on the CPU oracle and on the plain GPU
+path. Also: admission when the staging ring is small, and argument errors."""
+from __future__ import annotations
+
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1602_05232_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1602_05232_gb300 import _build, cc as ccmod
+    _build.build_cc()
+    ccmod.load()
+    return ccmod
+
+
+def make_trace(scale, m, seed, ulo=4, uhi=12, qlo=4, qhi=11):
+    s = I.rmat_stream(scale=scale, m=m, batch=m, q=1, seed=seed)
+    edges = s.all_edges()
+    reqs = I.request_trace(m, rate_hz=2000.0, seed=seed, ulo=ulo, uhi=uhi, qlo=qlo, qhi=qhi)
+    qtot = sum(r.size for r in reqs if r.kind == 1)
+    pairs = I.uniform_pairs(s.n, qtot, seed, I.TAG_QUERIES)
+    data = []
+    for r in reqs:
+        src = edges if r.kind == 0 else pairs
+        data.append(torch.from_numpy(src[r.offset:r.offset + r.size].copy()).pin_memory())
+    return s.n, reqs, data
+
+
+def alone_answers(n, reqs, data):
+    """Each request alone, in arrival order, on the oracle."""
+    uf = oracle.OracleUF(n)
+    want = {}
+    for i, (r, d) in enumerate(zip(reqs, data)):
+        if r.kind == 0:
+            uf.bulk_update(d.numpy())
+        else:
+            want[i] = uf.bulk_query(d.numpy())
+    return want, uf.labels()
+
+
+def serve(cc, n, reqs, data, paced=False, **cfg):
+    f = cc.Forest(n)
+    outs = {}
+    with cc.Server(f, **cfg) as srv:
+        t0 = time.perf_counter()
+        for i, (r, d) in enumerate(zip(reqs, data)):
+            if paced:
+                while time.perf_counter() - t0 < r.t:
+                    pass
+            out = None
+            if r.kind == 1:
+                out = torch.zeros(r.size, dtype=torch.uint8).pin_memory()
+                outs[i] = out
+            srv.enqueue(r.kind, d, out)
+        srv.drain()
+        lat = srv.latencies()
+        st = srv.stats()
+    labels = f.labels().cpu().numpy()
+    f.sync()
+    return {i: o.numpy() for i, o in outs.items()}, labels, lat, st
+
+
+@pytest.mark.parametrize("mode", ["burst", "paced", "no_merge", "tiny_ring"])
+def test_served_equals_alone(cc, mode):
+    n, reqs, data = make_trace(scale=16, m=1 << 19, seed=7)
+    want, want_labels = alone_answers(n, reqs, data)
+    cfg = {}
+    if mode == "no_merge":
+        cfg = {"merge": False}
+    if mode == "tiny_ring":
+        cfg = {"ring_pairs": 1 << 12, "max_group_pairs": 1 << 11}
+    got, labels, lat, st = serve(cc, n, reqs, data, paced=(mode == "paced"), **cfg)
+    for i, w in want.items():
+        assert np.array_equal(got[i], w), f"request {i} differs from running it alone"
+    assert np.array_equal(labels, want_labels)
+    assert st["completed"] == st["requests"] == len(reqs)
+    assert np.all(lat >= 0)
+    if mode == "burst":
+        assert st["groups"] < len(reqs)     # requests were merged
+    if mode == "no_merge":
+        assert st["groups"] == len(reqs)
+
+
+def test_served_equals_plain_gpu_alone(cc):
+    n, reqs, data = make_trace(scale=14, m=1 << 16, seed=8)
+    got, labels, _, _ = serve(cc, n, reqs, data)
+    f = cc.Forest(n)
+    for i, (r, d) in enumerate(zip(reqs, data)):
+        if r.kind == 0:
+            f.bulk_update(d.cuda())
+        else:
+            assert np.array_equal(f.bulk_query(d.cuda()).cpu().numpy(), got[i]), i
+    assert np.array_equal(f.labels().cpu().numpy(), labels)
+
+
+def test_concurrent_producers_keep_each_thread_order(cc):
+    # two client threads enqueue interleaved; the server's ticket order is the
+    # arrival order, and the answers match the oracle run in that order
+    n, reqs, data = make_trace(scale=14, m=1 << 17, seed=9)
+    f = cc.Forest(n)
+    tickets = [None] * len(reqs)
+    outs = {}
+    lock = threading.Lock()
+    with cc.Server(f) as srv:
+        def producer(idx):
+            for i in idx:
+                r, d = reqs[i], data[i]
+                out = torch.zeros(r.size, dtype=torch.uint8).pin_memory() if r.kind else None
+                with lock:
+                    tickets[i] = srv.enqueue(r.kind, d, out)
+                    if out is not None:
+                        outs[i] = out
+        th = [threading.Thread(target=producer, args=(list(range(j, len(reqs), 2)),)) for j in (0, 1)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        srv.drain()
+    order = sorted(range(len(reqs)), key=lambda i: tickets[i])
+    uf = oracle.OracleUF(n)
+    for i in order:
+        if reqs[i].kind == 0:
+            uf.bulk_update(data[i].numpy())
+        else:
+            assert np.array_equal(outs[i].numpy(), uf.bulk_query(data[i].numpy())), i
+
+
+def test_server_errors(cc):
+    f = cc.Forest(100)
+    with cc.Server(f, ring_pairs=64) as srv:
+        big = torch.zeros((65, 2), dtype=torch.int32)
+        with pytest.raises(cc.CCError) as ex:
+            srv.enqueue(cc.OP_UPDATE, big)
+        assert ex.value.status == cc.CC_ERR_ARG
+        with pytest.raises(TypeError):
+            srv.enqueue(cc.OP_QUERY, torch.zeros((3, 2), dtype=torch.int32), None)
+        t = srv.enqueue(cc.OP_UPDATE, torch.zeros((0, 2), dtype=torch.int32))
+        assert srv.wait(t) >= 0
+    # the handle is usable again after the server is gone
+    f.bulk_update(torch.tensor([[1, 2]], dtype=torch.int32, device="cuda"))
+    assert f.components() == 99
