@@ -21,9 +21,11 @@
  *  - Vertex ids are int32 in [0, n). An edge or a query pair is two int32s,
  *    stored flat as u0, v0, u1, v1, ... (8 bytes per pair). A pointer of 16-
  *    byte alignment gets 16-byte vector loads; 4-byte alignment is the minimum.
- *  - Array arguments are DEVICE pointers owned by the caller unless stated
- *    otherwise. They must stay valid until the handle's stream has executed
- *    the call (calls are asynchronous).
+ *  - Array arguments are DEVICE-ACCESSIBLE pointers owned by the caller
+ *    unless stated otherwise: device memory, or pinned host memory mapped for
+ *    the device (see cc_device_can_read), which the kernels then read and
+ *    write directly over the host link. They must stay valid until the
+ *    handle's stream has executed the call (calls are asynchronous).
  *  - All work is enqueued in order on the handle's stream, so each bulk
  *    operation completes before the next one starts (the paper's ordering
  *    rule, Section 1). A handle must not be used from two host threads at once.
@@ -333,6 +335,13 @@ cc_status cc_kernel_stats(cc_ctx* ctx, uint64_t* launches, double* ms);
 #define CC_STATIC_MAX_VERTICES (1 << 22)
 cc_status cc_components_static(const int32_t* edges, int64_t k, int64_t n, int32_t* labels,
                                uint32_t* status, cc_stream_t stream);
+
+/* *ok = 1 if kernels on the current device can read `p` directly: device or
+ * managed memory, or host memory that is pinned and mapped into the device's
+ * address space (on a Grace-Blackwell node the kernels then read it over
+ * NVLink-C2C). Every array argument of the bulk entry points may be such
+ * host memory; check it with this call first. *ok = 0 otherwise. */
+cc_status cc_device_can_read(const void* p, int32_t* ok);
 
 int64_t cc_num_vertices(const cc_ctx* ctx);
 const char* cc_status_string(cc_status s);

@@ -85,6 +85,7 @@ def load(path: str | Path | None = None) -> ctypes.CDLL:
         "cc_server_get_stats": [vp, vp],
         "cc_server_latencies": [vp, vp, i64, ctypes.POINTER(ctypes.c_int64)],
         "cc_server_destroy": [vp],
+        "cc_device_can_read": [vp, ctypes.POINTER(ctypes.c_int32)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -107,9 +108,19 @@ def check(status: int, L: ctypes.CDLL | None = None) -> None:
         raise CCError(status, (L.cc_last_error_string() or b"").decode())
 
 
+def device_can_read(t: torch.Tensor) -> bool:
+    """True if libcc's kernels can read this tensor's memory directly (device
+    memory, or pinned host memory mapped for the device)."""
+    ok = ctypes.c_int32()
+    check(load().cc_device_can_read(t.data_ptr(), ctypes.byref(ok)))
+    return bool(ok.value)
+
+
 def _pairs_ptr(t: torch.Tensor, name: str) -> tuple[int, int]:
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise TypeError(f"{name}: expected a CUDA tensor")
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a tensor")
+    if not t.is_cuda and not (t.is_pinned() and device_can_read(t)):
+        raise TypeError(f"{name}: expected a CUDA tensor or device-readable pinned host memory")
     if t.dtype != torch.int32 or not t.is_contiguous():
         raise TypeError(f"{name}: expected a contiguous int32 tensor")
     if t.numel() % 2:
@@ -189,9 +200,12 @@ class Forest:
     def bulk_query(self, pairs: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         p, k = _pairs_ptr(pairs, "pairs")
         if out is None:
-            out = torch.empty(k, dtype=torch.uint8, device=pairs.device)
-        if out.dtype != torch.uint8 or not out.is_contiguous() or out.numel() < k or not out.is_cuda:
-            raise TypeError("out: expected a contiguous CUDA uint8 tensor of k elements")
+            out = (torch.empty(k, dtype=torch.uint8, device=pairs.device) if pairs.is_cuda
+                   else torch.empty(k, dtype=torch.uint8, pin_memory=True))
+        if out.dtype != torch.uint8 or not out.is_contiguous() or out.numel() < k:
+            raise TypeError("out: expected a contiguous uint8 tensor of k elements")
+        if k and not out.is_cuda and not (out.is_pinned() and device_can_read(out)):
+            raise TypeError("out: expected CUDA or device-readable pinned host memory")
         check(self._L.cc_bulk_query(self._h, p, k, out.data_ptr()), self._L)
         return out
 

@@ -709,4 +709,19 @@ cc_status cc_kernel_stats(cc_ctx* c, uint64_t* launches, double* ms) {
 
 int64_t cc_num_vertices(const cc_ctx* c) { return c ? c->n : 0; }
 
+cc_status cc_device_can_read(const void* p, int32_t* ok) {
+    if (!ok) return fail(CC_ERR_ARG, "cc_device_can_read: ok is null");
+    *ok = 0;
+    if (!p) return CC_OK;
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return CC_OK;
+    }
+    if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) *ok = 1;
+    else if (attr.type == cudaMemoryTypeHost && attr.devicePointer == p) *ok = 1;
+    return CC_OK;
+}
+
 }  // extern "C"

@@ -1,0 +1,228 @@
+"""Autotuner for libcc's launch options.
+
+Picks, per workload and device, the options that minimise the time of one
+pass over a workload's minibatch stream:
+  * plain form: Bulk-Update kernel variant, edges (pairs) per thread, block
+    size, how often cc_bulk_update runs the full compression pass, and
+    whether Bulk-Query halves paths;
+  * batched form: CTA size, edges per thread, the shared-memory graph-size
+    cap (which also sets how many CTAs fit on an SM) and the persistent
+    grid size.
+
+The search is coordinate descent from a starting point: each parameter in
+turn is swept with the others fixed, keeping the best, for a few rounds; the
+best few configurations seen are then re-timed and the fastest wins. Every
+evaluation is the median of `repeats` passes timed with CUDA events on the
+forest's stream, each pass starting from an empty forest (reset not timed).
+
+Results are cached in ``tuned.json`` next to this file, keyed by device name
+and workload; ``tuned_options()`` reads them. Run as a module on the GPU to
+(re)tune: ``python -m paper_1602_05232_gb300.tune --workload rmat --write``.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import statistics
+from pathlib import Path
+
+import numpy as np
+import torch
+
+from . import cc
+from . import inputs as I
+
+CACHE = Path(__file__).resolve().parent / "tuned.json"
+
+PLAIN_SPACE = {
+    "update_variant": [0, 1, 2],
+    "edges_per_thread": [1, 2, 4],
+    "block": [128, 256, 512, 1024],
+    "compress_every": [0, 1, 2, 4, 8, 16],
+    "compress_scope": [0, 1],
+    "query_halving": [0, 1],
+}
+PLAIN_START = {"update_variant": 0, "edges_per_thread": 2, "block": 256, "compress_every": 1,
+               "compress_scope": 0, "query_halving": 0}
+
+SEG_SPACE = {
+    "seg_block": [128, 256, 512, 1024],
+    "seg_edges_per_thread": [1, 2, 4],
+    "seg_smem_cap": [65536, 32768, 16384],
+    "seg_max_ctas": [0, 152, 304],
+}
+SEG_START = {"seg_block": 512, "seg_edges_per_thread": 1, "seg_smem_cap": 65536,
+             "seg_max_ctas": 0, "seg_graph": 1}
+
+
+def device_name() -> str:
+    return torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+
+
+def tuned_options(workload: str, device: str | None = None) -> dict | None:
+    """Cached best options for `workload` on `device` (default: the current
+    CUDA device), or None."""
+    try:
+        d = json.loads(CACHE.read_text())
+        return dict(d[device or device_name()][workload]["options"])
+    except Exception:
+        return None
+
+
+def _store(workload: str, best: dict, ms: float, table: list) -> None:
+    d = json.loads(CACHE.read_text()) if CACHE.exists() else {}
+    d.setdefault(device_name(), {})[workload] = {
+        "options": best, "ms_per_pass": round(ms, 4),
+        "evaluated": [{"options": o, "ms": round(t, 4)} for o, t in sorted(table, key=lambda x: x[1])[:12]],
+    }
+    CACHE.write_text(json.dumps(d, indent=1, sort_keys=True) + "\n")
+
+
+def coordinate_descent(space: dict, start: dict, evaluate, rounds: int = 2, finalists: int = 3,
+                       log=None) -> tuple[dict, float, list]:
+    """Minimise evaluate(options) over the product space by sweeping one
+    parameter at a time. Returns (best options, time, [(options, time)])."""
+    seen: dict[str, float] = {}
+
+    def ev(o):
+        key = json.dumps(o, sort_keys=True)
+        if key not in seen:
+            seen[key] = evaluate(o)
+            if log:
+                log(o, seen[key])
+        return seen[key]
+
+    best = dict(start)
+    best_t = ev(best)
+    for _ in range(rounds):
+        improved = False
+        for name, values in space.items():
+            for v in values:
+                cand = dict(best, **{name: v})
+                t = ev(cand)
+                if t < best_t:
+                    best, best_t, improved = cand, t, True
+        if not improved:
+            break
+    table = [(json.loads(k), t) for k, t in seen.items()]
+    top = sorted(table, key=lambda x: x[1])[:finalists]
+    retimed = [(o, min(t, evaluate(o))) for o, t in top]
+    best, best_t = min(retimed, key=lambda x: x[1])
+    return best, best_t, table
+
+
+# ------------------------------------------------------------ plain form
+
+class PlainBench:
+    """A minibatch stream resident on the device, timed pass by pass."""
+
+    def __init__(self, stream_obj, device="cuda"):
+        self.s = stream_obj
+        self.d_e = torch.from_numpy(stream_obj.all_edges()).to(device)
+        self.d_q = torch.from_numpy(stream_obj.all_queries()).to(device)
+        self.d_o = torch.empty(stream_obj.q, dtype=torch.uint8, device=device)
+        self.eoff = stream_obj.edge_offsets()
+        self.qoff = stream_obj.query_offsets()
+        self.cuda_stream = torch.cuda.Stream()
+
+    def time(self, options: dict, repeats: int = 3) -> float:
+        st = self.cuda_stream
+        with torch.cuda.stream(st):
+            f = cc.Forest(self.s.n, stream=st, **options)
+            times = []
+            for r in range(repeats + 1):
+                f.reset()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                for i in range(self.s.batches):
+                    f.bulk_update(self.d_e[self.eoff[i]:self.eoff[i + 1]])
+                    f.bulk_query(self.d_q[self.qoff[i]:self.qoff[i + 1]],
+                                 out=self.d_o[self.qoff[i]:self.qoff[i + 1]])
+                b.record(st)
+                st.synchronize()
+                if r:  # the first pass warms up
+                    times.append(a.elapsed_time(b))
+            f.sync()
+            f.close()
+        return statistics.median(times)
+
+
+def tune_plain(stream_obj, space=PLAIN_SPACE, start=PLAIN_START, repeats: int = 3, log=None):
+    bench = PlainBench(stream_obj)
+    return coordinate_descent(space, start, lambda o: bench.time(o, repeats), log=log)
+
+
+# ---------------------------------------------------------- batched form
+
+class SegmentedBench:
+    def __init__(self, w, device="cuda"):
+        self.w = w
+        self.d_e, self.d_q, self.ops = [], [], []
+        m_all = w.total_edges
+        self.out = torch.empty(m_all, dtype=torch.uint8, device=device)
+        base = 0
+        for g in range(w.G):
+            self.d_e.append(torch.from_numpy(w.edges(g)).to(device))
+            self.d_q.append(torch.from_numpy(w.queries(g)).to(device))
+            for kind, off, k in w.ops(g):
+                src = self.d_e[g] if kind == 0 else self.d_q[g]
+                self.ops.append((g, kind, src.data_ptr() + 8 * off, k,
+                                 self.out.data_ptr() + base + off if kind == 1 else 0))
+            base += w.m(g)
+        self.ops = np.array(self.ops, dtype=cc.OP_DTYPE)
+        self.cuda_stream = torch.cuda.Stream()
+
+    def time(self, options: dict, repeats: int = 5) -> float:
+        st = self.cuda_stream
+        with torch.cuda.stream(st):
+            f = cc.Forest.segmented(self.w.n, stream=st, **options)
+            times = []
+            for r in range(repeats + 1):
+                f.reset()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                f.submit(self.ops)
+                b.record(st)
+                st.synchronize()
+                if r:
+                    times.append(a.elapsed_time(b))
+            f.sync()
+            f.close()
+        return statistics.median(times)
+
+
+def tune_segmented(w, space=SEG_SPACE, start=SEG_START, repeats: int = 5, log=None):
+    bench = SegmentedBench(w)
+    return coordinate_descent(space, start, lambda o: bench.time(o, repeats), log=log)
+
+
+WORKLOADS = {
+    "rmat": lambda: ("plain", I.rmat_stream()),
+    "grid": lambda: ("plain", I.grid_stream()),
+    "uniform": lambda: ("plain", I.uniform_stream()),
+    "serving": lambda: ("plain", I.rmat_stream(scale=26, m=1 << 28, batch=1 << 20, q=1 << 18)),
+    "segmented": lambda: ("segmented", I.segmented_workload()),
+}
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description="tune libcc launch options on this GPU")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), action="append", required=True)
+    ap.add_argument("--write", action="store_true", help="store the result in tuned.json")
+    args = ap.parse_args(argv)
+    for wl in args.workload:
+        form, obj = WORKLOADS[wl]()
+        log = lambda o, t: print(f"  {wl}: {t:9.3f} ms  {o}", flush=True)
+        if form == "plain":
+            best, t, table = tune_plain(obj, log=log)
+        else:
+            best, t, table = tune_segmented(obj, log=log)
+        print(json.dumps({"workload": wl, "device": device_name(), "best": best,
+                          "ms_per_pass": round(t, 4), "evaluated": len(table)}), flush=True)
+        if args.write:
+            _store(wl, best, t, table)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
