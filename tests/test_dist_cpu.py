@@ -1,0 +1,56 @@
+"""bench.py's multi-rank logic on CPU with two gloo ranks: the max/sum
+reductions used for the timing (no data-path collective), and the reference
+arm running on rank 0 only."""
+from __future__ import annotations
+
+import os
+import socket
+import sys
+from pathlib import Path
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank: int, world: int, port: int, q) -> None:
+    sys.path.insert(0, str(ROOT))
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import bench
+    r, w, lr = bench.dist_env()
+    dist = bench.dist_init(w, "gloo")
+    bench.dist_barrier(dist)
+    mx = bench.dist_max(dist, float(10 + rank))
+    sm = bench.dist_sum(dist, float(1 + rank))
+    import argparse
+    ns = argparse.Namespace(workload="uniform", steps=4, warmup=3, ref_fraction=64)
+    ref = bench.run_reference(ns, r, w)
+    q.put((r, mx, sm, ref is None, None if ref is None else ref.get("impl")))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [x[1] for x in res] == [11.0, 11.0]          # max over ranks
+    assert [x[2] for x in res] == [3.0, 3.0]            # sum over ranks
+    assert res[0][3] is False and res[0][4] == "reference"   # rank 0 runs the reference arm
+    assert res[1][3] is True                             # rank 1 does no work
