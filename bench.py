@@ -53,6 +53,10 @@ LAUNCH_OPTIONS = {
                   "seg_graph": 1},
     "serving": {"block": 256, "edges_per_thread": 4, "update_variant": 2, "compress_every": 0,
                 "compress_scope": 0},
+    "paper-random": {"block": 256, "edges_per_thread": 4, "update_variant": 2, "compress_every": 0},
+    "paper-rmat5": {"block": 256, "edges_per_thread": 4, "update_variant": 2, "compress_every": 0},
+    "paper-rmat16": {"block": 256, "edges_per_thread": 4, "update_variant": 2, "compress_every": 0},
+    "paper-3dgrid": {"block": 256, "edges_per_thread": 2, "update_variant": 2, "compress_every": 2},
 }
 
 
@@ -428,6 +432,81 @@ def run_serving(args, rank: int, world: int, local_rank: int, dist) -> dict:
     }
 
 
+# ------------------------------------------------- paper-scale streams (Table 3)
+
+# Bulk-Update throughput on 20 cores, M edges/s at b = 500K / 1M / 5M / 10M
+# (Table 3), for the graphs these streams stand in for.
+PAPER_T20C = {"random": [36.87, 46.02, 60.66, 63.90], "rmat5": [26.08, 34.19, 49.92, 50.37],
+              "3dgrid": [27.97, 34.97, 44.27, 45.24], "rmat16": [54.94, 78.10, 143.63, 167.68]}
+PAPER_BATCHES = [500_000, 1_000_000, 5_000_000, 10_000_000]
+
+
+def run_paper(args, rank: int, world: int, local_rank: int, dist) -> dict:
+    """Bulk-Update throughput (total edges / total update time, as in Table 3)
+    on a paper-size stream at the paper's four batch sizes, and the number of
+    connected components at every tenth of the stream (the Figure 2 curve)."""
+    import torch
+    from paper_1602_05232_gb300 import cc, inputs as I
+
+    name = args.workload.split("-", 1)[1]
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    s0 = I.paper_stream(name, batch=PAPER_BATCHES[-1], seed=rank)
+    d_edges = torch.from_numpy(s0.all_edges()).to(dev)
+    opts = launch_options(args.workload)
+    stream = torch.cuda.Stream(device=dev)
+    per_batch = {}
+    with torch.cuda.stream(stream):
+        f = cc.Forest(s0.n, stream=stream, **opts)
+        for b in PAPER_BATCHES:
+            cuts = list(range(0, s0.m, b)) + [s0.m]
+
+            def one_pass():
+                f.reset()
+                for i in range(len(cuts) - 1):
+                    f.bulk_update(d_edges[cuts[i]:cuts[i + 1]])
+            one_pass()
+            stream.synchronize()
+            times = []
+            for _ in range(max(1, min(args.steps, 3))):
+                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                f.reset()
+                stream.synchronize()
+                a.record(stream)
+                for i in range(len(cuts) - 1):
+                    f.bulk_update(d_edges[cuts[i]:cuts[i + 1]])
+                e.record(stream)
+                stream.synchronize()
+                times.append(a.elapsed_time(e))
+            per_batch[b] = s0.m / (statistics.median(times) / 1e3)
+        # component count at every tenth of the stream, b = 10M
+        f.reset()
+        curve, b = [], PAPER_BATCHES[-1]
+        cuts = list(range(0, s0.m, b)) + [s0.m]
+        marks = {int(round(s0.m * t / 10)) for t in range(1, 11)}
+        done = 0
+        for i in range(len(cuts) - 1):
+            f.bulk_update(d_edges[cuts[i]:cuts[i + 1]])
+            done = cuts[i + 1]
+            if any(cuts[i] < mk <= done for mk in marks):
+                curve.append([round(100.0 * done / s0.m, 1), f.components()])
+        f.sync()
+        f.close()
+    t20 = PAPER_T20C[name]
+    return {
+        "metric": "Bulk-Update edges/s (Table 3 shape: total edges / total update time)",
+        "value": round(per_batch[PAPER_BATCHES[-1]], 1), "unit": "edges/s", "n_gpus": world,
+        "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": s0.name, "n": s0.n, "m": s0.m, "options": opts,
+                   "stands_in_for": name},
+        "bulk_update_edges_per_s": {str(b): round(v, 1) for b, v in per_batch.items()},
+        "paper_T20c_edges_per_s": {str(b): t * 1e6 for b, t in zip(PAPER_BATCHES, t20)},
+        "ratio_to_paper_20c": {str(b): round(per_batch[b] / (t * 1e6), 1)
+                               for b, t in zip(PAPER_BATCHES, t20)},
+        "components_curve": curve,
+    }
+
+
 # --------------------------------------------------------------- GPU arm
 
 def run_gpu(args, rank: int, world: int, local_rank: int, dist) -> dict | None:
@@ -770,7 +849,8 @@ def main(argv=None) -> int:
     ap.add_argument("--steps", type=int, default=5120)
     ap.add_argument("--warmup", type=int, default=16)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", choices=sorted(LAUNCH_OPTIONS), default="rmat")
+    ap.add_argument("--workload", choices=sorted(LAUNCH_OPTIONS) + [
+        "paper-random", "paper-rmat5", "paper-rmat16", "paper-3dgrid"], default="rmat")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-fraction", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
@@ -789,6 +869,8 @@ def main(argv=None) -> int:
             out = run_segmented(args, rank, world, local_rank, dist)
         elif args.workload == "serving":
             out = run_serving(args, rank, world, local_rank, dist)
+        elif args.workload.startswith("paper-"):
+            out = run_paper(args, rank, world, local_rank, dist)
         else:
             out = run_gpu(args, rank, world, local_rank, dist)
         if dist is not None:

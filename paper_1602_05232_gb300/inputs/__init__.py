@@ -49,6 +49,8 @@ def lib() -> ctypes.CDLL:
         L.gen_shuffle_pairs.argtypes = [u64, u64, i64, p]
         L.gen_grid_edges.argtypes = [i64, i64, p]
         L.gen_grid_edges.restype = i64
+        L.gen_grid3d_edges.argtypes = [i64, i64, i64, p]
+        L.gen_grid3d_edges.restype = i64
         L.gen_unit.argtypes = [u64, u64, i64, i64, p]
         L.gen_u64.argtypes = [u64, u64, i64, i64, p]
         L.gen_set_threads.argtypes = [i32]
@@ -105,6 +107,14 @@ def grid_edges(rows: int, cols: int) -> np.ndarray:
     return out
 
 
+def grid3d_edges(a: int, b: int, c: int) -> np.ndarray:
+    m = a * b * (c - 1) + a * (b - 1) * c + (a - 1) * b * c
+    out = np.empty((m, 2), dtype=np.int32)
+    got = lib().gen_grid3d_edges(a, b, c, _ptr(out))
+    assert got == m
+    return out
+
+
 def shuffle_pairs(pairs: np.ndarray, seed: int, tag: int = TAG_SHUFFLE) -> np.ndarray:
     assert pairs.dtype == np.int32 and pairs.flags.c_contiguous
     lib().gen_shuffle_pairs(seed, tag, pairs.shape[0], _ptr(pairs))
@@ -134,6 +144,7 @@ class PlainStream:
     abc: tuple[float, float, float] = (0.57, 0.19, 0.19)
     rows: int = 0
     cols: int = 0
+    depth: int = 0
     _perm: np.ndarray | None = field(default=None, repr=False)
     _grid: np.ndarray | None = field(default=None, repr=False)
 
@@ -160,7 +171,8 @@ class PlainStream:
 
     def grid(self) -> np.ndarray:
         if self._grid is None:
-            g = grid_edges(self.rows, self.cols)
+            g = (grid3d_edges(self.rows, self.cols, self.depth) if self.depth
+                 else grid_edges(self.rows, self.cols))
             self._grid = shuffle_pairs(g, self.seed, TAG_SHUFFLE)
         return self._grid
 
@@ -239,6 +251,37 @@ def grid_stream(rows: int = 8192, cols: int = 8192, batch: int = 1 << 22,
     ups = [min(batch, m - i * batch) for i in range(nb)]
     return PlainStream(f"grid {rows}x{cols} b={batch}", "grid", rows * cols, ups, [q] * nb,
                        seed, rows=rows, cols=cols)
+
+
+def grid3d_stream(a: int = 464, b: int = 464, c: int = 464, batch: int = 10_000_000,
+                  q: int = 1 << 20, seed: int = 0) -> PlainStream:
+    """6-neighbour a x b x c mesh, edges Fisher-Yates shuffled. Default
+    464^3: 99.9 M vertices and 299 M edges, the size of the paper's 3Dgrid
+    (Table 1)."""
+    m = a * b * (c - 1) + a * (b - 1) * c + (a - 1) * b * c
+    nb = -(-m // batch)
+    ups = [min(batch, m - i * batch) for i in range(nb)]
+    return PlainStream(f"grid3d {a}x{b}x{c} b={batch}", "grid", a * b * c, ups, [q] * nb,
+                       seed, rows=a, cols=b, depth=c)
+
+
+# Paper-scale stand-ins for Table 1 (the paper's own generators are not
+# available): sizes match, structure follows the named generator family.
+def paper_stream(name: str, batch: int, q: int = 0, seed: int = 0) -> PlainStream:
+    """'random': 10^8 vertices, 5x10^8 edges with i.i.d. uniform endpoints
+    (the paper's random graph has 5 random neighbours per vertex);
+    'rmat5': R-MAT scale 27 (134 M vertices), 5x10^8 edges; 'rmat16': the
+    same with 1.6x10^9 edges; '3dgrid': the 464^3 mesh (99.9 M vertices,
+    299 M edges)."""
+    if name == "random":
+        return uniform_stream(n=100_000_000, m=500_000_000, batch=batch, q=q, seed=seed)
+    if name == "rmat5":
+        return rmat_stream(scale=27, m=500_000_000, batch=batch, q=q, seed=seed)
+    if name == "rmat16":
+        return rmat_stream(scale=27, m=1_600_000_000, batch=batch, q=q, seed=seed)
+    if name == "3dgrid":
+        return grid3d_stream(batch=batch, q=q, seed=seed)
+    raise ValueError(name)
 
 
 # --------------------------------------------------------- segmented graphs

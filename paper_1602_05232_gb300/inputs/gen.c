@@ -201,6 +201,22 @@ int64_t gen_grid_edges(int64_t rows, int64_t cols, int32_t* out) {
     return e;
 }
 
+/* 6-neighbour 3-D grid of a x b x c vertices, id = (i*b + j)*c + k. Edges in
+ * id order of their lower endpoint: +k, then +j, then +i neighbours. Returns
+ * the number written: a*b*(c-1) + a*(b-1)*c + (a-1)*b*c. */
+int64_t gen_grid3d_edges(int64_t a, int64_t b, int64_t c, int32_t* out) {
+    int64_t e = 0;
+    for (int64_t i = 0; i < a; i++)
+        for (int64_t j = 0; j < b; j++)
+            for (int64_t k = 0; k < c; k++) {
+                int64_t v = (i * b + j) * c + k;
+                if (k + 1 < c) { out[2 * e] = (int32_t)v; out[2 * e + 1] = (int32_t)(v + 1); e++; }
+                if (j + 1 < b) { out[2 * e] = (int32_t)v; out[2 * e + 1] = (int32_t)(v + c); e++; }
+                if (i + 1 < a) { out[2 * e] = (int32_t)v; out[2 * e + 1] = (int32_t)(v + b * c); e++; }
+            }
+    return e;
+}
+
 /* ------------------------------------------------------ scalar draws */
 
 /* count doubles uniform in [0, 1), draw i from counter offset+i. */

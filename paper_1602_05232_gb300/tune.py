@@ -202,6 +202,9 @@ WORKLOADS = {
     "uniform": lambda: ("plain", I.uniform_stream()),
     "serving": lambda: ("plain", I.rmat_stream(scale=26, m=1 << 28, batch=1 << 20, q=1 << 18)),
     "segmented": lambda: ("segmented", I.segmented_workload()),
+    "paper-random": lambda: ("plain", I.paper_stream("random", batch=10_000_000, q=1)),
+    "paper-rmat5": lambda: ("plain", I.paper_stream("rmat5", batch=10_000_000, q=1)),
+    "paper-3dgrid": lambda: ("plain", I.paper_stream("3dgrid", batch=10_000_000, q=1)),
 }
 
 

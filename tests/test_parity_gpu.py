@@ -274,3 +274,20 @@ def test_full_size_grid_stream(cc):
     f, ref = _full_stream(cc, s, launch_options("grid"), label_batches={0, s.batches // 2})
     lab = f.labels()
     assert int(lab.max()) == 0 and f.components() == 1 == ref.components
+
+
+def test_paper_scale_random_stream_component_curve(cc):
+    # 10^8 vertices, 5x10^8 uniform edges in minibatches of 10^7 (the paper's
+    # largest batch, Table 3): component count after every minibatch (the
+    # Figure 2 curve) and the final labels against the oracle
+    from bench import launch_options
+    s = I.paper_stream("random", batch=10_000_000, q=1)
+    f = cc.Forest(s.n, **launch_options("paper-random"))
+    ref = oracle.OracleUF(s.n)
+    for i in range(s.batches):
+        e = s.edges(i)
+        f.bulk_update(dev(e))
+        ref.bulk_update(e)
+        assert f.components() == ref.components, f"component count at minibatch {i}"
+    assert np.array_equal(f.labels().cpu().numpy(), ref.labels())
+    f.sync()
