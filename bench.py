@@ -49,6 +49,7 @@ LAUNCH_OPTIONS = {
                 "compress_scope": 0},
     "grid": {"block": 256, "edges_per_thread": 2, "update_variant": 2, "compress_every": 4,
              "compress_scope": 0},
+    "hub": {"block": 256, "edges_per_thread": 4, "update_variant": 2, "compress_every": 0},
     "segmented": {"seg_block": 512, "seg_edges_per_thread": 1, "seg_smem_cap": 65536,
                   "seg_graph": 1},
     "serving": {"block": 256, "edges_per_thread": 4, "update_variant": 2, "compress_every": 0,
@@ -60,20 +61,27 @@ LAUNCH_OPTIONS = {
 }
 
 
+OPTION_OVERRIDES: dict = {}
+
+
 def launch_options(workload: str) -> dict:
     """Autotuned options for this device when cached (paper_1602_05232_gb300/
     tuned.json, written by ``python -m paper_1602_05232_gb300.tune``), else
-    the built-in defaults above."""
+    the built-in defaults above; ``--opt key=value`` overrides either."""
     try:
         from paper_1602_05232_gb300 import tune
         t = tune.tuned_options(workload)
     except Exception:
         t = None
-    return t if t is not None else dict(LAUNCH_OPTIONS[workload])
+    opts = t if t is not None else dict(LAUNCH_OPTIONS[workload])
+    opts.update(OPTION_OVERRIDES)
+    return opts
 
 
 def make_stream(workload: str, seed: int):
     from paper_1602_05232_gb300 import inputs as I
+    if workload == "hub":
+        return I.hub_stream(seed=seed)
     if workload == "rmat":
         return I.rmat_stream(seed=seed)
     if workload == "uniform":
@@ -90,6 +98,8 @@ WORKLOAD_TEXT = {
                "a Bulk-Query of 2^16 uniform pairs",
     "grid": "shuffled 8192x8192 4-neighbour grid (n=2^26, 134,201,344 edges) in 32 "
             "Bulk-Updates of 2^22, each followed by a Bulk-Query of 2^22 uniform pairs",
+    "hub": "star at scale: n=2^24, 2^27 edges (hub n-1, uniform vertex) in 128 Bulk-Updates of "
+           "2^20, each followed by a Bulk-Query of 2^20 uniform pairs",
     "segmented": "1024 graphs, n log-uniform in [2^8,2^16), m=4n uniform edges, minibatches "
                  "log-uniform in [2^6,2^14), each followed by a Bulk-Query of the same size",
     "serving": "request loop on one R-MAT n=2^26 stream (2^30 edges): Poisson arrivals, "
@@ -631,7 +641,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int, dist) -> dict | None:
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms_max / args.steps, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded R-MAT / uniform / grid generators; no dataset)",
-        "config": {"workload": WORKLOAD_TEXT[args.workload], "n": s.n, "edges_per_pass": s.m,
+        "config": {"workload": WORKLOAD_TEXT.get(args.workload, s.name), "n": s.n, "edges_per_pass": s.m,
                    "batch": int(eoff[1]), "query_batch": int(qoff[1]),
                    "form": "plain (one launch per bulk operation)", "options": opts,
                    "l2": "inputs larger than L2: 1 GiB edge + 1 GiB pair streams, each read "
@@ -855,11 +865,16 @@ def main(argv=None) -> int:
     ap.add_argument("--ref-fraction", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--opt", action="append", default=[], metavar="KEY=VALUE",
+                    help="override a libcc launch option (e.g. update_schedule=1)")
     ap.add_argument("--serve-scale", type=int, default=26,
                     help="R-MAT scale of the serving trace (2^(scale+4) edges)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    for kv in args.opt:
+        k, v = kv.split("=", 1)
+        OPTION_OVERRIDES[k] = int(v)
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world)

@@ -88,7 +88,13 @@ typedef enum {
     CC_OPT_SEG_GRAPH = 11,       /* batched form: 1 = capture the submit (table copy, queue reset,
                                     kernel) once as a CUDA graph and replay it (default 1) */
     CC_OPT_SEG_MAX_CTAS = 12,    /* batched form: cap on persistent CTAs (0 = one full wave, default) */
-    CC_OPT__COUNT = 13
+    CC_OPT_UPDATE_SCHEDULE = 13, /* Bulk-Update schedule: 0 = one fused find + CAS-hook kernel
+                                    (default); 1 = the paper's Algorithm 2 as written: relabel
+                                    and drop self-loops, connected components of the relabelled
+                                    edges (Shiloach-Vishkin rounds), then join each component's
+                                    roots under its smallest root. Schedule 1 synchronises once
+                                    per round. */
+    CC_OPT__COUNT = 14
 } cc_option;
 
 /* Kernel kinds reported by the launch counters and the profiler. */
@@ -335,6 +341,16 @@ cc_status cc_kernel_stats(cc_ctx* ctx, uint64_t* launches, double* ms);
 #define CC_STATIC_MAX_VERTICES (1 << 22)
 cc_status cc_components_static(const int32_t* edges, int64_t k, int64_t n, int32_t* labels,
                                uint32_t* status, cc_stream_t stream);
+
+/* Schedule 1 only (CC_OPT_UPDATE_SCHEDULE): for the last Bulk-Update, the
+ * number of relabelled edges that were not self-loops (|A''| of Algorithm 2)
+ * and the number of connected-components rounds it took. Host outputs. */
+cc_status cc_schedule_stats(cc_ctx* ctx, int64_t* nonloop_edges, int32_t* rounds);
+
+/* Schedule 1 only: copy the last Bulk-Update's A'' (pairs of distinct roots,
+ * in no particular order) to `out` (device, 2*cap int32); *count receives
+ * |A''| (the copy stops at cap pairs). Synchronises. */
+cc_status cc_copy_nonloop(cc_ctx* ctx, int32_t* out, int64_t cap, int64_t* count);
 
 /* *ok = 1 if kernels on the current device can read `p` directly: device or
  * managed memory, or host memory that is pinned and mapped into the device's

@@ -65,6 +65,8 @@ def _bind(L: ctypes.CDLL) -> ctypes.CDLL:
     L.oracle_bulk_query.restype = None
     L.oracle_labels.argtypes = [p, p]
     L.oracle_labels.restype = None
+    L.oracle_relabel.argtypes = [p, p, i64, p]
+    L.oracle_relabel.restype = i64
     for f in ("oracle_n", "oracle_unions", "oracle_errors", "oracle_components"):
         getattr(L, f).argtypes = [p]
         getattr(L, f).restype = i64
@@ -108,6 +110,16 @@ class OracleUF:
         self._L.oracle_bulk_query(self._h, q.ctypes.data_as(ctypes.c_void_p), q.shape[0],
                                   out.ctypes.data_as(ctypes.c_void_p))
         return out
+
+    def relabel(self, edges) -> np.ndarray:
+        """A'' of Algorithm 2 for these edges against the current graph:
+        (id(u), id(v)) with minimum-id component identifiers, self-loops
+        dropped, edge order kept. Does not add the edges."""
+        e = _pairs(edges)
+        out = np.empty((e.shape[0], 2), dtype=np.int32)
+        m = int(self._L.oracle_relabel(self._h, e.ctypes.data_as(ctypes.c_void_p), e.shape[0],
+                                       out.ctypes.data_as(ctypes.c_void_p)))
+        return out[:m]
 
     def labels(self) -> np.ndarray:
         """int32 labels: the minimum vertex id of each vertex's component."""

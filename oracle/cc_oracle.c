@@ -122,6 +122,30 @@ void oracle_labels(oracle_uf* u, int32_t* out) {
     free(mn);
 }
 
+/* Relabel and filter (Algorithm 2, the relabel step and the self-loop
+ * filter), for the edges about to be added: every edge (u, v) becomes
+ * (id(u), id(v)) where id is the component identifier before the minibatch,
+ * canonicalised to the smallest vertex id of the component; pairs with
+ * id(u) == id(v) are dropped. Writes the survivors (A'') to out, in edge
+ * order, and returns how many. Out-of-range edges are skipped. Does not add
+ * the edges. */
+int64_t oracle_relabel(oracle_uf* u, const int32_t* edges, int64_t k, int32_t* out) {
+    const int64_t n = u->n;
+    int32_t* lab = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    oracle_labels(u, lab);
+    int64_t m = 0;
+    for (int64_t i = 0; i < k; i++) {
+        int32_t a = edges[2 * i], b = edges[2 * i + 1];
+        if (!in_range(u, a) || !in_range(u, b)) continue;
+        if (lab[a] == lab[b]) continue;
+        out[2 * m] = lab[a];
+        out[2 * m + 1] = lab[b];
+        m++;
+    }
+    free(lab);
+    return m;
+}
+
 int64_t oracle_n(const oracle_uf* u) { return u->n; }
 int64_t oracle_unions(const oracle_uf* u) { return u->unions; }
 int64_t oracle_errors(const oracle_uf* u) { return u->errors; }

@@ -26,7 +26,7 @@ OPTIONS = {"block": OPT_BLOCK, "edges_per_thread": OPT_EDGES_PER_THREAD,
            "query_halving": OPT_QUERY_HALVING, "profile": OPT_PROFILE,
            "update_variant": OPT_UPDATE_VARIANT, "l2_persist": OPT_L2_PERSIST,
            "seg_block": 8, "seg_edges_per_thread": 9, "seg_smem_cap": 10, "seg_graph": 11,
-           "seg_max_ctas": 12}
+           "seg_max_ctas": 12, "update_schedule": 13}
 OP_UPDATE, OP_QUERY = 0, 1
 # Layout of cc_op (include/cc.h): graph, kind, data pointer, k, out pointer.
 OP_DTYPE = np.dtype([("graph", "<i4"), ("kind", "<i4"), ("data", "<u8"), ("k", "<i8"),
@@ -86,6 +86,8 @@ def load(path: str | Path | None = None) -> ctypes.CDLL:
         "cc_server_latencies": [vp, vp, i64, ctypes.POINTER(ctypes.c_int64)],
         "cc_server_destroy": [vp],
         "cc_device_can_read": [vp, ctypes.POINTER(ctypes.c_int32)],
+        "cc_schedule_stats": [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)],
+        "cc_copy_nonloop": [vp, vp, i64, ctypes.POINTER(ctypes.c_int64)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -238,6 +240,21 @@ class Forest:
         v = ctypes.c_int64()
         check(self._L.cc_components(self._h, ctypes.byref(v)), self._L)
         return v.value
+
+    def schedule_stats(self) -> tuple[int, int]:
+        """(|A''|, connected-components rounds) of the last Bulk-Update under
+        the paper's schedule (update_schedule=1)."""
+        m, r = ctypes.c_int64(), ctypes.c_int32()
+        check(self._L.cc_schedule_stats(self._h, ctypes.byref(m), ctypes.byref(r)), self._L)
+        return m.value, r.value
+
+    def nonloop_edges(self) -> torch.Tensor:
+        """A'' of the last Bulk-Update under the paper's schedule: (m, 2) int32."""
+        m, _ = self.schedule_stats()
+        out = torch.empty((max(m, 1), 2), dtype=torch.int32, device="cuda")
+        cnt = ctypes.c_int64()
+        check(self._L.cc_copy_nonloop(self._h, out.data_ptr(), m, ctypes.byref(cnt)), self._L)
+        return out[:m]
 
     def submit(self, ops) -> None:
         """Run bulk operations in one persistent launch (cc_submit). ``ops`` is

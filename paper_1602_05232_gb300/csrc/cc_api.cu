@@ -51,7 +51,7 @@ struct DeviceScope {
 };
 
 const int64_t kDefaults[CC_OPT__COUNT] = {256, 2, 1, CC_COMPRESS_ALL, 0, 0, 0, 0,
-                                          512, 1, 65536, 1, 0};
+                                          512, 1, 65536, 1, 0, 0};
 
 }  // namespace
 
@@ -85,6 +85,14 @@ struct cc_ctx {
     int64_t graph_key[5] = {-1, -1, -1, -1, -1};
     std::vector<int> bucket_count, op_begin_h, order_h;
     std::vector<int64_t> work_h;
+
+    // the paper's schedule (CC_OPT_UPDATE_SCHEDULE = 1)
+    int* a2 = nullptr;            // A'': compacted pairs of distinct roots
+    int64_t a2_cap = 0;           // in pairs
+    int* comp = nullptr;          // component labels of A'' endpoints (n entries)
+    unsigned* pcount = nullptr;   // device: [0] = |A''|, [1] = hooked flag
+    int64_t last_nonloop = 0;
+    int32_t last_rounds = 0;
 };
 
 namespace {
@@ -156,6 +164,71 @@ cc_status do_compress(cc_ctx* c, int scope, const int32_t* edges, int64_t k) {
     if (k == 0) return CC_OK;
     return run(c, CC_K_COMPRESS_TOUCHED, "compress(touched)", [&] {
         return cc::launch_compress_touched(c->parent, (int)c->n, edges, k, c->ds, cfg_of(c), c->stream);
+    });
+}
+
+// Algorithm 2 as written, one Bulk-Update: relabel + filter, CC rounds, join.
+cc_status paper_update(cc_ctx* c, const int32_t* edges, int64_t k) {
+    cudaError_t e = cudaSuccess;
+    if (!c->comp) {
+        e = cudaMalloc(&c->comp, sizeof(int) * (size_t)c->n);
+        if (e == cudaSuccess) e = cudaMalloc(&c->pcount, 2 * sizeof(unsigned));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CC_ERR_OOM, "schedule 1: component array of %lld entries", (long long)c->n);
+        }
+    }
+    if (k > c->a2_cap) {
+        int* a2 = nullptr;
+        e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess) e = cudaMalloc(&a2, sizeof(int) * 2 * (size_t)k);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CC_ERR_OOM, "schedule 1: A'' buffer of %lld pairs", (long long)k);
+        }
+        cudaFree(c->a2);
+        c->a2 = a2;
+        c->a2_cap = k;
+    }
+    const int block = (int)c->opt[CC_OPT_BLOCK];
+    cc_status st = run(c, CC_K_UPDATE, "schedule 1: relabel", [&]() -> cudaError_t {
+        cudaError_t e1 = cudaMemsetAsync(c->pcount, 0, 2 * sizeof(unsigned), c->stream);
+        if (e1 != cudaSuccess) return e1;
+        return cc::launch_relabel(c->parent, (int)c->n, edges, k, c->a2, c->pcount, c->comp, c->ds, block, c->stream);
+    });
+    if (st != CC_OK) return st;
+    unsigned m2 = 0;
+    e = cudaMemcpyAsync(&m2, c->pcount, sizeof m2, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "schedule 1: read |A''|");
+    c->last_nonloop = m2;
+    c->last_rounds = 0;
+    if (m2 == 0) return CC_OK;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    int64_t g = (2 * (int64_t)m2 + block - 1) / block;
+    const int grid = (int)(g < 8LL * sms ? g : 8LL * sms);
+    // each round with a hook removes at least one component root, so at most
+    // 2|A''| rounds can hook; the next one finds nothing to do
+    const int64_t max_rounds = 2 * (int64_t)m2 + 1;
+    for (int64_t r = 0;; r++) {
+        if (r >= max_rounds) return fail(CC_ERR_CORRUPT, "schedule 1: connected components did not converge");
+        unsigned hooked = 0;
+        st = run(c, CC_K_UPDATE, "schedule 1: components round", [&]() -> cudaError_t {
+            cudaError_t e1 = cudaMemsetAsync(c->pcount + 1, 0, sizeof(unsigned), c->stream);
+            if (e1 != cudaSuccess) return e1;
+            return cc::launch_sv_round(c->a2, c->pcount, c->comp, c->pcount + 1, grid, block, c->stream);
+        });
+        if (st != CC_OK) return st;
+        c->launches[CC_K_UPDATE]++;  // a round is two kernels: hook, then jump
+        e = cudaMemcpyAsync(&hooked, c->pcount + 1, sizeof hooked, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "schedule 1: read round flag");
+        c->last_rounds = (int32_t)(r + 1);
+        if (!hooked) break;
+    }
+    return run(c, CC_K_UPDATE, "schedule 1: join", [&] {
+        return cc::launch_join(c->a2, c->pcount, c->comp, c->parent, c->ds, grid, block, c->stream);
     });
 }
 
@@ -250,6 +323,9 @@ cc_status cc_destroy(cc_ctx* c) {
         if (c->staging) cudaFreeHost(c->staging);
         cudaFree(c->tables);
         cudaFree(c->seg_off);
+        cudaFree(c->a2);
+        cudaFree(c->comp);
+        cudaFree(c->pcount);
         cudaFree(c->parent);
         cudaFree(c->ds);
     }
@@ -302,9 +378,13 @@ cc_status cc_bulk_update(cc_ctx* c, const int32_t* edges, int64_t k) {
     if (c->G > 1) return fail(CC_ERR_UNSUPPORTED, "cc_bulk_update on a segmented handle: use cc_submit");
     if (k == 0) return CC_OK;
     CC_DEVICE(c);
-    s = run(c, CC_K_UPDATE, "bulk_update", [&] {
-        return cc::launch_update(c->parent, (int)c->n, edges, k, c->ds, cfg_of(c), c->stream);
-    });
+    if (c->opt[CC_OPT_UPDATE_SCHEDULE] == 1) {
+        s = paper_update(c, edges, k);
+    } else {
+        s = run(c, CC_K_UPDATE, "bulk_update", [&] {
+            return cc::launch_update(c->parent, (int)c->n, edges, k, c->ds, cfg_of(c), c->stream);
+        });
+    }
     if (s != CC_OK) return s;
     c->flat = false;
     c->update_calls++;
@@ -647,6 +727,9 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
         case CC_OPT_SEG_MAX_CTAS:
             if (value < 0 || value > (1 << 20)) return fail(CC_ERR_ARG, "seg max ctas %lld out of range", (long long)value);
             break;
+        case CC_OPT_UPDATE_SCHEDULE:
+            if (value != 0 && value != 1) return fail(CC_ERR_ARG, "update schedule %lld: need 0 or 1", (long long)value);
+            break;
         case CC_OPT_UPDATE_VARIANT:
             if (value < 0 || value > 2) return fail(CC_ERR_ARG, "update variant %lld: need 0, 1 or 2", (long long)value);
             break;
@@ -708,6 +791,26 @@ cc_status cc_kernel_stats(cc_ctx* c, uint64_t* launches, double* ms) {
 }
 
 int64_t cc_num_vertices(const cc_ctx* c) { return c ? c->n : 0; }
+
+cc_status cc_schedule_stats(cc_ctx* c, int64_t* nonloop_edges, int32_t* rounds) {
+    CC_CHECK_CTX(c);
+    if (nonloop_edges) *nonloop_edges = c->last_nonloop;
+    if (rounds) *rounds = c->last_rounds;
+    return CC_OK;
+}
+
+cc_status cc_copy_nonloop(cc_ctx* c, int32_t* out, int64_t cap, int64_t* count) {
+    CC_CHECK_CTX(c);
+    if (count) *count = c->last_nonloop;
+    const int64_t m = c->last_nonloop < cap ? c->last_nonloop : cap;
+    if (m <= 0) return CC_OK;
+    if (!out) return fail(CC_ERR_ARG, "cc_copy_nonloop: out is null");
+    CC_DEVICE(c);
+    cudaError_t e = cudaMemcpyAsync(out, c->a2, sizeof(int) * 2 * (size_t)m, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cc_copy_nonloop");
+    return CC_OK;
+}
 
 cc_status cc_device_can_read(const void* p, int32_t* ok) {
     if (!ok) return fail(CC_ERR_ARG, "cc_device_can_read: ok is null");

@@ -94,6 +94,15 @@ cudaError_t prepare_segmented(SegLaunch& cfg);
 cudaError_t launch_segmented(int* parent, const int64_t* seg_off, const SegTables& t,
                              unsigned* queue, DevState* ds, const SegLaunch& cfg, cudaStream_t s);
 
+// ---- the paper's Bulk-Update schedule (Algorithm 2 as written) ----
+
+cudaError_t launch_relabel(int* parent, int n, const int* edges, int64_t k, int* a2, unsigned* m2,
+                           int* comp, DevState* ds, int block, cudaStream_t s);
+cudaError_t launch_sv_round(const int* a2, const unsigned* m2, int* comp, unsigned* hooked,
+                            int grid, int block, cudaStream_t s);
+cudaError_t launch_join(const int* a2, const unsigned* m2, const int* comp, int* parent,
+                        DevState* ds, int grid, int block, cudaStream_t s);
+
 // Checks 0 <= lab[v] <= v and lab[lab[v]] == lab[v]; counts roots.
 cudaError_t launch_validate_labels(const int* lab, int64_t n, DevState* ds, int block,
                                    cudaStream_t s);

@@ -145,6 +145,7 @@ class PlainStream:
     rows: int = 0
     cols: int = 0
     depth: int = 0
+    hub: int = -1
     _perm: np.ndarray | None = field(default=None, repr=False)
     _grid: np.ndarray | None = field(default=None, repr=False)
 
@@ -185,6 +186,10 @@ class PlainStream:
             a, b, c = self.abc
             return rmat_edges(self.scale, k, a, b, c, self.seed, TAG_EDGES, lo,
                               self.perm(), out)
+        if self.kind == "hub":
+            out = uniform_pairs(self.n, k, self.seed, TAG_EDGES, lo, out)
+            out[:k, 0] = self.hub
+            return out
         if self.kind == "grid":
             src = self.grid()[lo:hi]
             if out is None:
@@ -238,6 +243,17 @@ def rmat_stream(scale: int = 24, m: int = 1 << 27, batch: int = 1 << 20,
     ups = [min(batch, m - i * batch) for i in range(nb)]
     return PlainStream(f"rmat scale={scale} m={m} b={batch}", "rmat", 1 << scale, ups,
                        [q] * nb, seed, scale=scale, abc=abc)
+
+
+def hub_stream(n: int = 1 << 24, m: int = 1 << 27, batch: int = 1 << 20, q: int = 1 << 20,
+               hub: int | None = None, seed: int = 0) -> PlainStream:
+    """Every edge joins one hub vertex (default the largest id) to a uniform
+    random vertex: the star of Section 3.2 at scale, the worst case for
+    concurrent hooking onto one root."""
+    nb = -(-m // batch)
+    ups = [min(batch, m - i * batch) for i in range(nb)]
+    h = n - 1 if hub is None else hub
+    return PlainStream(f"hub n={n} m={m} b={batch} hub={h}", "hub", n, ups, [q] * nb, seed, hub=h)
 
 
 def grid_stream(rows: int = 8192, cols: int = 8192, batch: int = 1 << 22,

@@ -274,8 +274,40 @@ def pin_range_rule(lib) -> list[str]:
     return fails
 
 
+def pin_relabel(lib) -> list[str]:
+    """A'' (Algorithm 2's relabel + self-loop filter) against BFS labels on
+    tiny streams, and the star minibatch closed form (Section 3.2)."""
+    fails = []
+    for seed in range(120):
+        r = _rng(5000 + seed)
+        n = int(r.integers(1, 30))
+        uf = _uf(lib, n)
+        seen = []
+        for b in range(4):
+            e = r.integers(0, n, size=(int(r.integers(0, 2 * n + 1)), 2)).astype(np.int32)
+            lab = bfs_labels(n, seen)
+            want = [(lab[u], lab[v]) for u, v in e.tolist() if lab[u] != lab[v]]
+            got = [tuple(x) for x in uf.relabel(e).tolist()]
+            if got != want:
+                fails.append(f"relabel seed={seed} batch={b}")
+                break
+            uf.bulk_update(e)
+            seen += [tuple(x) for x in e.tolist()]
+    g = load_golden("star_minibatch.txt")
+    star = np.array(g["edges"], dtype=np.int32)
+    uf = _uf(lib, g["n"])
+    if uf.relabel(star).tolist() != star.tolist():
+        fails.append("star: on the empty graph A'' is the minibatch itself")
+    uf.bulk_update(star)
+    if len(uf.relabel(star)) != 0:
+        fails.append("star: repeating the minibatch leaves only self-loops")
+    if uf.relabel(np.array([[0, 8]], dtype=np.int32)).tolist() != [[0, 1]]:
+        fails.append("star: an edge into the star relabels to the star's smallest id")
+    return fails
+
+
 ALL_PINS = [pin_bfs_tiny, pin_scipy, pin_star, pin_closed_forms,
-            pin_order_independence, pin_invariants, pin_range_rule]
+            pin_order_independence, pin_invariants, pin_range_rule, pin_relabel]
 
 
 def run_all(lib) -> list[str]:

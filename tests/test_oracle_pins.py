@@ -26,16 +26,16 @@ def test_oracle_pin(lib, pin):
 # (description, exact text in cc_oracle.c, replacement, occurrence index)
 MUTANTS = [
     ("drops the last edge of every minibatch",
-     "for (int64_t i = 0; i < k; i++) {\n        int32_t a = edges",
-     "for (int64_t i = 0; i + 1 < k; i++) {\n        int32_t a = edges"),
+     "int64_t made = 0;\n    for (int64_t i = 0; i < k; i++) {",
+     "int64_t made = 0;\n    for (int64_t i = 0; i + 1 < k; i++) {"),
     ("unions already-connected roots instead of distinct ones",
      "if (ra == rb) continue;", "if (ra != rb) continue;"),
     ("query compares an endpoint with itself",
      "out[i] = (uint8_t)(find(u, a) == find(u, b));",
      "out[i] = (uint8_t)(find(u, a) == find(u, a));"),
     ("reads the first endpoint twice",
-     "int32_t a = edges[2 * i], b = edges[2 * i + 1];",
-     "int32_t a = edges[2 * i], b = edges[2 * i];"),
+     "int32_t a = edges[2 * i], b = edges[2 * i + 1];\n        if (!in_range(u, a) || !in_range(u, b)) { u->errors++;",
+     "int32_t a = edges[2 * i], b = edges[2 * i];\n        if (!in_range(u, a) || !in_range(u, b)) { u->errors++;"),
     ("labels keep the maximum id",
      "if (v < mn[r]) mn[r] = (int32_t)v;", "if (mn[r] == INT32_MAX || v > mn[r]) mn[r] = (int32_t)v;"),
     ("compression cuts a node loose",
@@ -46,6 +46,10 @@ MUTANTS = [
      "return u->n - u->unions;", "return u->n;"),
     ("forgets the link when ranks are equal",
      "u->p[rb] = ra;\n            u->rank[ra]++;", "u->rank[ra]++;"),
+    ("relabel keeps self-loops",
+     "if (lab[a] == lab[b]) continue;", "if (lab[a] == lab[b] && a < 0) continue;"),
+    ("relabel writes the endpoint instead of its identifier",
+     "out[2 * m + 1] = lab[b];", "out[2 * m + 1] = b;"),
 ]
 
 
