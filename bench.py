@@ -589,6 +589,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int, dist) -> dict | None:
         # (C) per-kernel events for the roofline
         _, _, kstats, launches0, launches1 = region(False, True)
     gpu_launches = sum(la1[k] - la0[k] for k in la1)
+    depth_max, depth_mean = f.depth()
     f.sync()
 
     total_ms_max = dist_max(dist, total_ms, dev)
@@ -656,6 +657,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int, dist) -> dict | None:
                                "second pass of the K steps with an event after each step"},
         "timing": "value from K steps between two events with nothing else recorded; latency "
                   "and the per-kernel times (roofline) from two more passes over the same K steps",
+        "forest_depth": {"max": depth_max, "mean": round(depth_mean, 4),
+                         "what": "distance from a vertex to its root after the timed steps"},
         "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
         "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu,
     }

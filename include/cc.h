@@ -94,7 +94,13 @@ typedef enum {
                                     edges (Shiloach-Vishkin rounds), then join each component's
                                     roots under its smallest root. Schedule 1 synchronises once
                                     per round. */
-    CC_OPT__COUNT = 14
+    CC_OPT_LINK = 14,            /* 0 = link by index: the larger root goes under the smaller
+                                    (default; parent[v] <= v always, roots are component minima);
+                                    1 = union by size (Section 3, Lemma 1: trees stay O(log n) high;
+                                    needs CC_OPT_UPDATE_SCHEDULE = 1, whose join step is
+                                    conflict-free). Settable only while the forest has no edges;
+                                    not for segmented handles. */
+    CC_OPT__COUNT = 15
 } cc_option;
 
 /* Kernel kinds reported by the launch counters and the profiler. */
@@ -351,6 +357,11 @@ cc_status cc_schedule_stats(cc_ctx* ctx, int64_t* nonloop_edges, int32_t* rounds
  * in no particular order) to `out` (device, 2*cap int32); *count receives
  * |A''| (the copy stops at cap pairs). Synchronises. */
 cc_status cc_copy_nonloop(cc_ctx* ctx, int32_t* out, int64_t cap, int64_t* count);
+
+/* Height of the forest: *max_depth (host) = the longest path from a vertex
+ * to its root, *mean_depth (host, may be NULL) = the mean over all vertices.
+ * A diagnostic for the link rules (CC_OPT_LINK). Synchronises. */
+cc_status cc_forest_depth(cc_ctx* ctx, int32_t* max_depth, double* mean_depth);
 
 /* *ok = 1 if kernels on the current device can read `p` directly: device or
  * managed memory, or host memory that is pinned and mapped into the device's

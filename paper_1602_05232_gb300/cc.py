@@ -26,7 +26,7 @@ OPTIONS = {"block": OPT_BLOCK, "edges_per_thread": OPT_EDGES_PER_THREAD,
            "query_halving": OPT_QUERY_HALVING, "profile": OPT_PROFILE,
            "update_variant": OPT_UPDATE_VARIANT, "l2_persist": OPT_L2_PERSIST,
            "seg_block": 8, "seg_edges_per_thread": 9, "seg_smem_cap": 10, "seg_graph": 11,
-           "seg_max_ctas": 12, "update_schedule": 13}
+           "seg_max_ctas": 12, "update_schedule": 13, "link": 14}
 OP_UPDATE, OP_QUERY = 0, 1
 # Layout of cc_op (include/cc.h): graph, kind, data pointer, k, out pointer.
 OP_DTYPE = np.dtype([("graph", "<i4"), ("kind", "<i4"), ("data", "<u8"), ("k", "<i8"),
@@ -88,6 +88,7 @@ def load(path: str | Path | None = None) -> ctypes.CDLL:
         "cc_device_can_read": [vp, ctypes.POINTER(ctypes.c_int32)],
         "cc_schedule_stats": [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)],
         "cc_copy_nonloop": [vp, vp, i64, ctypes.POINTER(ctypes.c_int64)],
+        "cc_forest_depth": [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -240,6 +241,12 @@ class Forest:
         v = ctypes.c_int64()
         check(self._L.cc_components(self._h, ctypes.byref(v)), self._L)
         return v.value
+
+    def depth(self) -> tuple[int, float]:
+        """(max, mean) distance from a vertex to its root."""
+        mx, mean = ctypes.c_int32(), ctypes.c_double()
+        check(self._L.cc_forest_depth(self._h, ctypes.byref(mx), ctypes.byref(mean)), self._L)
+        return mx.value, mean.value
 
     def schedule_stats(self) -> tuple[int, int]:
         """(|A''|, connected-components rounds) of the last Bulk-Update under

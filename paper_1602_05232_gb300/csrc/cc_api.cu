@@ -51,7 +51,7 @@ struct DeviceScope {
 };
 
 const int64_t kDefaults[CC_OPT__COUNT] = {256, 2, 1, CC_COMPRESS_ALL, 0, 0, 0, 0,
-                                          512, 1, 65536, 1, 0, 0};
+                                          512, 1, 65536, 1, 0, 0, 0};
 
 }  // namespace
 
@@ -93,6 +93,11 @@ struct cc_ctx {
     unsigned* pcount = nullptr;   // device: [0] = |A''|, [1] = hooked flag
     int64_t last_nonloop = 0;
     int32_t last_rounds = 0;
+
+    // union by size (CC_OPT_LINK = 1)
+    int* size = nullptr;                 // tree sizes, meaningful at roots
+    unsigned long long* best = nullptr;  // per-component vote of the join step
+    bool fresh = true;                   // no edge since create / reset
 };
 
 namespace {
@@ -154,6 +159,14 @@ cc_status check_pairs(const int32_t* p, int64_t k, const char* name) {
 }
 
 cc_status do_compress(cc_ctx* c, int scope, const int32_t* edges, int64_t k) {
+    if (c->opt[CC_OPT_LINK] == 1) {  // union by size: only the full generic pass
+        cc_status s = run(c, CC_K_COMPRESS_ALL, "compress(all, generic)", [&] {
+            return cc::launch_compress_generic(c->parent, c->n, nullptr, nullptr, c->ds,
+                                               (int)c->opt[CC_OPT_BLOCK], c->stream);
+        });
+        if (s == CC_OK) c->flat = true;
+        return s;
+    }
     if (scope == CC_COMPRESS_ALL) {
         cc_status s = run(c, CC_K_COMPRESS_ALL, "compress(all)", [&] {
             return cc::launch_compress_all(c->parent, c->n, nullptr, c->ds, (int)c->opt[CC_OPT_BLOCK], c->stream);
@@ -194,6 +207,9 @@ cc_status paper_update(cc_ctx* c, const int32_t* edges, int64_t k) {
     cc_status st = run(c, CC_K_UPDATE, "schedule 1: relabel", [&]() -> cudaError_t {
         cudaError_t e1 = cudaMemsetAsync(c->pcount, 0, 2 * sizeof(unsigned), c->stream);
         if (e1 != cudaSuccess) return e1;
+        if (c->opt[CC_OPT_LINK] == 1)
+            return cc::launch_relabel_generic(c->parent, (int)c->n, edges, k, c->a2, c->pcount, c->comp,
+                                              c->best, c->ds, block, c->stream);
         return cc::launch_relabel(c->parent, (int)c->n, edges, k, c->a2, c->pcount, c->comp, c->ds, block, c->stream);
     });
     if (st != CC_OK) return st;
@@ -227,10 +243,19 @@ cc_status paper_update(cc_ctx* c, const int32_t* edges, int64_t k) {
         c->last_rounds = (int32_t)(r + 1);
         if (!hooked) break;
     }
+    if (c->opt[CC_OPT_LINK] == 1) {
+        c->launches[CC_K_UPDATE]++;  // vote, then join
+        return run(c, CC_K_UPDATE, "schedule 1: size join", [&] {
+            return cc::launch_size_join(c->a2, c->pcount, c->comp, c->parent, c->size, c->best, c->ds,
+                                        grid, block, c->stream);
+        });
+    }
     return run(c, CC_K_UPDATE, "schedule 1: join", [&] {
         return cc::launch_join(c->a2, c->pcount, c->comp, c->parent, c->ds, grid, block, c->stream);
     });
 }
+
+bool by_size(const cc_ctx* c) { return c->opt[CC_OPT_LINK] == 1; }
 
 }  // namespace
 
@@ -326,6 +351,8 @@ cc_status cc_destroy(cc_ctx* c) {
         cudaFree(c->a2);
         cudaFree(c->comp);
         cudaFree(c->pcount);
+        cudaFree(c->size);
+        cudaFree(c->best);
         cudaFree(c->parent);
         cudaFree(c->ds);
     }
@@ -367,6 +394,11 @@ cc_status cc_reset(cc_ctx* c) {
     if (s == CC_OK) {
         c->flat = true;
         c->update_calls = 0;
+        c->fresh = true;
+        if (c->size) {
+            cudaError_t e2 = cc::launch_fill(c->size, c->n, 1, c->stream);
+            if (e2 != cudaSuccess) return cuda_fail(e2, "cc_reset: sizes");
+        }
     }
     return s;
 }
@@ -378,6 +410,9 @@ cc_status cc_bulk_update(cc_ctx* c, const int32_t* edges, int64_t k) {
     if (c->G > 1) return fail(CC_ERR_UNSUPPORTED, "cc_bulk_update on a segmented handle: use cc_submit");
     if (k == 0) return CC_OK;
     CC_DEVICE(c);
+    if (by_size(c) && c->opt[CC_OPT_UPDATE_SCHEDULE] != 1)
+        return fail(CC_ERR_UNSUPPORTED, "union by size (CC_OPT_LINK = 1) needs CC_OPT_UPDATE_SCHEDULE = 1");
+    c->fresh = false;
     if (c->opt[CC_OPT_UPDATE_SCHEDULE] == 1) {
         s = paper_update(c, edges, k);
     } else {
@@ -401,6 +436,15 @@ cc_status cc_bulk_query(cc_ctx* c, const int32_t* pairs, int64_t k, uint8_t* out
     if (k > 0 && !out) return fail(CC_ERR_ARG, "cc_bulk_query: out is null");
     if (k == 0) return CC_OK;
     CC_DEVICE(c);
+    if (by_size(c)) {
+        const bool flat = c->flat;
+        s = run(c, CC_K_QUERY, "bulk_query(generic)", [&] {
+            return cc::launch_query_generic(c->parent, (int)c->n, pairs, k, out, c->ds, flat,
+                                            (int)c->opt[CC_OPT_BLOCK], c->stream);
+        });
+        if (s == CC_OK && !flat) c->flat = false;
+        return s;
+    }
     const int mode = c->flat ? 2 : (c->opt[CC_OPT_QUERY_HALVING] ? 1 : 0);
     s = run(c, CC_K_QUERY, "bulk_query", [&] {
         return cc::launch_query(c->parent, (int)c->n, pairs, k, out, c->ds, mode, cfg_of(c), c->stream);
@@ -427,6 +471,18 @@ cc_status cc_labels(cc_ctx* c, int32_t* out) {
     if (!out) return fail(CC_ERR_ARG, "cc_labels: out is null");
     if (reinterpret_cast<uintptr_t>(out) % 4 != 0) return fail(CC_ERR_ARG, "cc_labels: out not 4-byte aligned");
     CC_DEVICE(c);
+    if (by_size(c)) {
+        if (!c->comp) {
+            cudaError_t e = cudaMalloc(&c->comp, sizeof(int) * (size_t)c->n);
+            if (e != cudaSuccess) { cudaGetLastError(); return fail(CC_ERR_OOM, "cc_labels: scratch"); }
+        }
+        cc_status s = run(c, CC_K_LABELS, "labels(generic)", [&] {
+            return cc::launch_compress_generic(c->parent, c->n, out, c->comp, c->ds,
+                                               (int)c->opt[CC_OPT_BLOCK], c->stream);
+        });
+        if (s == CC_OK) c->flat = true;
+        return s;
+    }
     cc_status s = run(c, CC_K_LABELS, "labels", [&] {
         return cc::launch_compress_all(c->parent, c->n, out, c->ds, (int)c->opt[CC_OPT_BLOCK], c->stream);
     });
@@ -459,6 +515,12 @@ cc_status cc_load_labels(cc_ctx* c, const int32_t* labels) {
     if (e != cudaSuccess) return cuda_fail(e, "cc_load_labels: copy");
     c->flat = true;
     c->update_calls = 0;
+    c->fresh = false;
+    if (by_size(c)) {
+        e = cc::launch_size_count(c->parent, c->n, c->size, c->ds, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cc_load_labels: sizes");
+    }
     return CC_OK;
 }
 
@@ -585,6 +647,7 @@ cc_status cc_submit(cc_ctx* c, const cc_op* ops, int64_t nops) {
     if (nops < 0 || nops > INT32_MAX) return fail(CC_ERR_ARG, "cc_submit: nops out of range");
     if (nops == 0) return CC_OK;
     if (!ops) return fail(CC_ERR_ARG, "cc_submit: ops is null");
+    if (by_size(c)) return fail(CC_ERR_UNSUPPORTED, "cc_submit with union by size");
     for (int64_t i = 0; i < nops; i++) {
         const cc_op& o = ops[i];
         if (o.graph < 0 || o.graph >= c->G) return fail(CC_ERR_ARG, "cc_submit: op %lld: graph %d out of [0, %d)", (long long)i, o.graph, c->G);
@@ -690,6 +753,7 @@ cc_status cc_submit(cc_ctx* c, const cc_op* ops, int64_t nops) {
     });
     if (st == CC_OK) c->staging_pending = true;
     c->flat = false;
+    c->fresh = false;
     return st;
 }
 
@@ -727,6 +791,21 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
         case CC_OPT_SEG_MAX_CTAS:
             if (value < 0 || value > (1 << 20)) return fail(CC_ERR_ARG, "seg max ctas %lld out of range", (long long)value);
             break;
+        case CC_OPT_LINK: {
+            if (value != 0 && value != 1) return fail(CC_ERR_ARG, "link %lld: need 0 (index) or 1 (size)", (long long)value);
+            if (value == c->opt[CC_OPT_LINK]) break;
+            if (!c->fresh) return fail(CC_ERR_ARG, "the link rule can only change while the forest has no edges (after create or reset)");
+            if (c->G > 1) return fail(CC_ERR_UNSUPPORTED, "union by size on a segmented handle");
+            if (value == 1) {
+                DeviceScope scope(c->device);
+                cudaError_t e = cudaSuccess;
+                if (!c->size) e = cudaMalloc(&c->size, sizeof(int) * (size_t)c->n);
+                if (e == cudaSuccess && !c->best) e = cudaMalloc(&c->best, sizeof(unsigned long long) * (size_t)c->n);
+                if (e == cudaSuccess) e = cc::launch_fill(c->size, c->n, 1, c->stream);
+                if (e != cudaSuccess) { cudaGetLastError(); return fail(CC_ERR_OOM, "union by size: size arrays"); }
+            }
+            break;
+        }
         case CC_OPT_UPDATE_SCHEDULE:
             if (value != 0 && value != 1) return fail(CC_ERR_ARG, "update schedule %lld: need 0 or 1", (long long)value);
             break;
@@ -809,6 +888,22 @@ cc_status cc_copy_nonloop(cc_ctx* c, int32_t* out, int64_t cap, int64_t* count) 
     cudaError_t e = cudaMemcpyAsync(out, c->a2, sizeof(int) * 2 * (size_t)m, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cc_copy_nonloop");
+    return CC_OK;
+}
+
+cc_status cc_forest_depth(cc_ctx* c, int32_t* max_depth, double* mean_depth) {
+    CC_CHECK_CTX(c);
+    if (!max_depth) return fail(CC_ERR_ARG, "cc_forest_depth: max_depth is null");
+    CC_DEVICE(c);
+    cudaError_t e = cudaMemsetAsync(&c->ds->max_depth, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&c->ds->sum_depth, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = cc::launch_depth(c->parent, c->n, &c->ds->max_depth, &c->ds->sum_depth, c->ds, c->stream);
+    cc::DevState h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, c->ds, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cc_forest_depth");
+    *max_depth = (int32_t)h.max_depth;
+    if (mean_depth) *mean_depth = (double)h.sum_depth / (double)c->n;
     return CC_OK;
 }
 

@@ -21,7 +21,8 @@ struct DevState {
     unsigned long long unions;  // successful hooks since create / reset
     unsigned long long roots;   // roots counted by the label validator
     unsigned queue;             // work-queue counter of the batched form
-    unsigned pad;
+    unsigned max_depth;         // forest height diagnostic
+    unsigned long long sum_depth;
 };
 
 struct Launch {
@@ -102,6 +103,24 @@ cudaError_t launch_sv_round(const int* a2, const unsigned* m2, int* comp, unsign
                             int grid, int block, cudaStream_t s);
 cudaError_t launch_join(const int* a2, const unsigned* m2, const int* comp, int* parent,
                         DevState* ds, int grid, int block, cudaStream_t s);
+
+// Union by size (the paper's schedule only) and the walks for forests that
+// do not keep parent[v] <= v.
+cudaError_t launch_relabel_generic(int* parent, int n, const int* edges, int64_t k, int* a2,
+                                   unsigned* m2, int* comp, unsigned long long* best, DevState* ds,
+                                   int block, cudaStream_t s);
+cudaError_t launch_size_join(const int* a2, const unsigned* m2, const int* comp, int* parent,
+                             int* size, unsigned long long* best, DevState* ds, int grid, int block,
+                             cudaStream_t s);
+cudaError_t launch_fill(int* a, int64_t n, int value, cudaStream_t s);
+cudaError_t launch_size_count(const int* parent, int64_t n, int* size, DevState* ds, cudaStream_t s);
+cudaError_t launch_query_generic(int* parent, int n, const int* pairs, int64_t k, uint8_t* out,
+                                 DevState* ds, bool flat, int block, cudaStream_t s);
+// Full compression; with labels_out also the minimum-id labels (uses minid_scratch, n ints).
+cudaError_t launch_compress_generic(int* parent, int64_t n, int* labels_out, int* minid_scratch,
+                                    DevState* ds, int block, cudaStream_t s);
+cudaError_t launch_depth(const int* parent, int64_t n, unsigned* max_depth,
+                         unsigned long long* sum_depth, DevState* ds, cudaStream_t s);
 
 // Checks 0 <= lab[v] <= v and lab[lab[v]] == lab[v]; counts roots.
 cudaError_t launch_validate_labels(const int* lab, int64_t n, DevState* ds, int block,

@@ -138,3 +138,244 @@ cudaError_t launch_join(const int* a2, const unsigned* m2, const int* comp, int*
 }
 
 }  // namespace cc
+
+// ---------------------------------------------------------------------------
+// Union by size (Section 3: the tree with fewer vertices goes under the one
+// with more, which keeps every tree O(log n) high, Lemma 1). Only the paper's
+// schedule can link this way without locks: within one minibatch each root
+// of A'' is linked at most once, under its component's winner, which is not
+// itself linked. Forests built this way no longer satisfy parent[v] <= v, so
+// they are walked with the generic loops below (p != x), each capped at n
+// steps: a longer walk can only mean a cycle, which is reported, not followed.
+// ---------------------------------------------------------------------------
+
+namespace cc {
+
+namespace {
+
+__device__ __forceinline__ int gfind(int* parent, int x, int n, DevState* ds) {
+    int p = parent[x];
+    for (int steps = 0; p != x; steps++) {
+        if (steps > n) {
+            flag(ds, ST_CORRUPT);
+            return x;
+        }
+        const int gp = parent[p];
+        if (gp == p) return p;
+        parent[x] = gp;  // halving
+        x = gp;
+        p = parent[x];
+    }
+    return x;
+}
+
+__device__ __forceinline__ int groot(const int* parent, int x, int n, DevState* ds) {
+    int p = parent[x];
+    for (int steps = 0; p != x; steps++) {
+        if (steps > n) {
+            flag(ds, ST_CORRUPT);
+            return x;
+        }
+        x = p;
+        p = parent[x];
+    }
+    return x;
+}
+
+__global__ void __launch_bounds__(1024)
+k_relabel_generic(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
+                  int* __restrict__ a2, unsigned* __restrict__ m2, int* __restrict__ comp,
+                  unsigned long long* __restrict__ best, DevState* __restrict__ ds) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool has = false;
+    int ru = 0, rv = 0;
+    if (i < k) {
+        int u[1], v[1];
+        load_pairs<1>(edges, i, k, vec, u, v);
+        if (in_range(u[0], n) && in_range(v[0], n)) {
+            ru = gfind(parent, u[0], n, ds);
+            rv = gfind(parent, v[0], n, ds);
+            if (ru != rv) {
+                has = true;
+                comp[ru] = ru;
+                comp[rv] = rv;
+                best[ru] = 0ull;
+                best[rv] = 0ull;
+            }
+        } else {
+            flag(ds, ST_RANGE);
+        }
+    }
+    append_pair(has, ru, rv, a2, m2);
+}
+
+// The vote key orders roots by size, then by smaller id.
+__device__ __forceinline__ unsigned long long vote_key(int size, int x) {
+    return ((unsigned long long)(unsigned)size << 32) | (unsigned long long)(0xffffffffu - (unsigned)x);
+}
+
+__global__ void __launch_bounds__(1024)
+k_size_vote(const int* __restrict__ a2, const unsigned* __restrict__ m2, const int* __restrict__ comp,
+            const int* __restrict__ size, unsigned long long* __restrict__ best) {
+    const unsigned m2x2 = 2u * *m2;
+    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < m2x2; j += gridDim.x * blockDim.x) {
+        const int x = a2[j];
+        atomicMax(best + comp[x], vote_key(size[x], x));
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+k_size_join(const int* __restrict__ a2, const unsigned* __restrict__ m2, const int* __restrict__ comp,
+            const unsigned long long* __restrict__ best, int* __restrict__ parent,
+            int* __restrict__ size, DevState* __restrict__ ds) {
+    const unsigned m2x2 = 2u * *m2;
+    int made = 0;
+    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < m2x2; j += gridDim.x * blockDim.x) {
+        const int x = a2[j];
+        const int w = (int)(0xffffffffu - (unsigned)(best[comp[x]] & 0xffffffffull));
+        if (w != x && atomicCAS(parent + x, x, w) == x) {
+            atomicAdd(size + w, size[x]);  // x is no longer a root: its size is final
+            made++;
+        }
+    }
+    made = __reduce_add_sync(0xffffffffu, made);
+    if ((threadIdx.x & 31) == 0 && made) atomicAdd(&ds->unions, (unsigned long long)made);
+}
+
+__global__ void __launch_bounds__(1024) k_fill(int* __restrict__ a, int64_t n, int value) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) a[v] = value;
+}
+
+// Sizes of a forest loaded from labels: every vertex adds one to its root.
+__global__ void __launch_bounds__(1024)
+k_size_count(const int* __restrict__ parent, int64_t n, int* __restrict__ size, DevState* ds) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) atomicAdd(size + groot(parent, (int)v, (int)n, ds), 1);
+}
+
+// Bulk-Query on any acyclic forest. FLAT: every tree has height <= 1.
+template <bool FLAT>
+__global__ void __launch_bounds__(1024)
+k_query_generic(int* __restrict__ parent, int n, const int* __restrict__ pairs, int64_t k, int vec,
+                uint8_t* __restrict__ out, DevState* __restrict__ ds) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k) return;
+    int u[1], v[1];
+    load_pairs<1>(pairs, i, k, vec, u, v);
+    uint8_t a = 0;
+    if (in_range(u[0], n) && in_range(v[0], n)) {
+        if (FLAT) a = (uint8_t)(parent[u[0]] == parent[v[0]]);
+        else a = (uint8_t)(gfind(parent, u[0], n, ds) == gfind(parent, v[0], n, ds));
+    } else {
+        flag(ds, ST_RANGE);
+    }
+    out[i] = a;
+}
+
+// Full compression on any acyclic forest; with MINID also the min-id reduce.
+template <bool MINID>
+__global__ void __launch_bounds__(1024)
+k_compress_generic(int* __restrict__ parent, int64_t n, int* __restrict__ minid, DevState* ds) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int r = groot(parent, (int)v, (int)n, ds);
+    if (parent[v] != r) parent[v] = r;
+    if (MINID) atomicMin(minid + r, (int)v);
+}
+
+__global__ void __launch_bounds__(1024)
+k_labels_generic(const int* __restrict__ parent, int64_t n, const int* __restrict__ minid,
+                 int* __restrict__ out) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) out[v] = minid[parent[v]];  // parent[v] is v's root after the compression
+}
+
+__global__ void __launch_bounds__(1024)
+k_depth(const int* __restrict__ parent, int64_t n, unsigned* __restrict__ max_depth,
+        unsigned long long* __restrict__ sum_depth, DevState* ds) {
+    const int64_t v0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned d = 0;
+    if (v0 < n) {
+        int x = (int)v0, p = parent[x];
+        while (p != x && d <= (unsigned)n) {
+            x = p;
+            p = parent[x];
+            d++;
+        }
+        if (d > (unsigned)n) flag(ds, ST_CORRUPT);
+    }
+    const unsigned mx = __reduce_max_sync(0xffffffffu, d);
+    const unsigned sm = __reduce_add_sync(0xffffffffu, d);
+    if ((threadIdx.x & 31) == 0) {
+        if (mx) atomicMax(max_depth, mx);
+        if (sm) atomicAdd(sum_depth, (unsigned long long)sm);
+    }
+}
+
+}  // namespace
+
+static inline unsigned grid1(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+cudaError_t launch_relabel_generic(int* parent, int n, const int* edges, int64_t k, int* a2,
+                                   unsigned* m2, int* comp, unsigned long long* best, DevState* ds,
+                                   int block, cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    k_relabel_generic<<<grid1(k, block), block, 0, s>>>(parent, n, edges, k, pair_vec(edges), a2, m2,
+                                                        comp, best, ds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_size_join(const int* a2, const unsigned* m2, const int* comp, int* parent,
+                             int* size, unsigned long long* best, DevState* ds, int grid, int block,
+                             cudaStream_t s) {
+    k_size_vote<<<grid, block, 0, s>>>(a2, m2, comp, size, best);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_size_join<<<grid, block, 0, s>>>(a2, m2, comp, best, parent, size, ds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(int* a, int64_t n, int value, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_fill<<<grid1(n, 256), 256, 0, s>>>(a, n, value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_size_count(const int* parent, int64_t n, int* size, DevState* ds, cudaStream_t s) {
+    cudaError_t e = launch_fill(size, n, 0, s);
+    if (e != cudaSuccess) return e;
+    k_size_count<<<grid1(n, 256), 256, 0, s>>>(parent, n, size, ds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_query_generic(int* parent, int n, const int* pairs, int64_t k, uint8_t* out,
+                                 DevState* ds, bool flat, int block, cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    if (flat) k_query_generic<true><<<grid1(k, block), block, 0, s>>>(parent, n, pairs, k, pair_vec(pairs), out, ds);
+    else k_query_generic<false><<<grid1(k, block), block, 0, s>>>(parent, n, pairs, k, pair_vec(pairs), out, ds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compress_generic(int* parent, int64_t n, int* labels_out, int* minid_scratch,
+                                    DevState* ds, int block, cudaStream_t s) {
+    if (!labels_out) {
+        k_compress_generic<false><<<grid1(n, block), block, 0, s>>>(parent, n, nullptr, ds);
+        return cudaGetLastError();
+    }
+    cudaError_t e = launch_fill(minid_scratch, n, 0x7fffffff, s);
+    if (e != cudaSuccess) return e;
+    k_compress_generic<true><<<grid1(n, block), block, 0, s>>>(parent, n, minid_scratch, ds);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_labels_generic<<<grid1(n, block), block, 0, s>>>(parent, n, minid_scratch, labels_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_depth(const int* parent, int64_t n, unsigned* max_depth,
+                         unsigned long long* sum_depth, DevState* ds, cudaStream_t s) {
+    k_depth<<<grid1(n, 256), 256, 0, s>>>(parent, n, max_depth, sum_depth, ds);
+    return cudaGetLastError();
+}
+
+}  // namespace cc
