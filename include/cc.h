@@ -100,7 +100,11 @@ typedef enum {
                                     needs CC_OPT_UPDATE_SCHEDULE = 1, whose join step is
                                     conflict-free). Settable only while the forest has no edges;
                                     not for segmented handles. */
-    CC_OPT__COUNT = 15
+    CC_OPT_BULK_FIND = 15,       /* 1: Bulk-Query, and the relabel step of CC_OPT_UPDATE_SCHEDULE = 1,
+                                    find all their roots with ONE Bulk-Find (Algorithm 4), whose
+                                    path compression is shared by the whole minibatch (Theorem 3).
+                                    Synchronises once per tree level. Default 0 */
+    CC_OPT__COUNT = 16
 } cc_option;
 
 /* Kernel kinds reported by the launch counters and the profiler. */
@@ -357,6 +361,29 @@ cc_status cc_schedule_stats(cc_ctx* ctx, int64_t* nonloop_edges, int32_t* rounds
  * in no particular order) to `out` (device, 2*cap int32); *count receives
  * |A''| (the copy stops at cap pairs). Synchronises. */
 cc_status cc_copy_nonloop(cc_ctx* ctx, int32_t* out, int64_t cap, int64_t* count);
+
+/* Bulk-Find (Algorithm 4; Section 4): res[i] = the root of S[i] for k
+ * vertices `S` (device, k int32; an id outside [0, n) gives -1 and is
+ * reported by cc_sync), with path compression shared by all of them:
+ * afterwards every vertex on a path from some S[i] to its root points at that
+ * root, and no other parent changes. Phase I walks up from all of S at once,
+ * merging flows that meet; the Response Distributor (hashing into 3|R_u|
+ * buckets and a counting sort, Section 4.1) lets Phase II hand each root back
+ * down the recorded paths. `res`: device, k int32. Synchronises once per
+ * level. */
+cc_status cc_bulk_find(cc_ctx* ctx, const int32_t* S, int64_t k, int32_t* res);
+
+/* For the last Bulk-Find: the number of traversed non-root vertices
+ * (|R_u| without R_0), and the number of Phase I and Phase II levels. */
+cc_status cc_bulk_find_stats(cc_ctx* ctx, int64_t* traversed, int32_t* levels_up,
+                             int32_t* levels_down);
+
+/* Replace the forest by an arbitrary one (device, n int32) with
+ * 0 <= parent[v] <= v for every v -- the invariant of the default link rule,
+ * which also rules out cycles. Synchronises. CC_ERR_LABELS (forest unchanged)
+ * if the array breaks it; CC_ERR_UNSUPPORTED under union by size or on a
+ * segmented handle. */
+cc_status cc_load_forest(cc_ctx* ctx, const int32_t* parent);
 
 /* Height of the forest: *max_depth (host) = the longest path from a vertex
  * to its root, *mean_depth (host, may be NULL) = the mean over all vertices.

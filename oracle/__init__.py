@@ -67,6 +67,8 @@ def _bind(L: ctypes.CDLL) -> ctypes.CDLL:
     L.oracle_labels.restype = None
     L.oracle_relabel.argtypes = [p, p, i64, p]
     L.oracle_relabel.restype = i64
+    L.oracle_bulk_find.argtypes = [i64, p, p, i64, p, p]
+    L.oracle_bulk_find.restype = i64
     for f in ("oracle_n", "oracle_unions", "oracle_errors", "oracle_components"):
         getattr(L, f).argtypes = [p]
         getattr(L, f).restype = i64
@@ -138,3 +140,20 @@ class OracleUF:
     @property
     def components(self) -> int:
         return int(self._L.oracle_components(self._h))
+
+
+def bulk_find(parent, S, lib: ctypes.CDLL | None = None):
+    """Bulk-Find (Algorithm 4) on the forest `parent`: returns (new parent
+    array, res = root of each S[i], number of traversed non-root nodes)."""
+    L = lib if lib is not None else load()
+    par = np.ascontiguousarray(parent, dtype=np.int32)
+    q = np.ascontiguousarray(S, dtype=np.int32)
+    out = np.empty_like(par)
+    res = np.empty(q.size, dtype=np.int32)
+    t = int(L.oracle_bulk_find(par.size, par.ctypes.data_as(ctypes.c_void_p),
+                               q.ctypes.data_as(ctypes.c_void_p), q.size,
+                               out.ctypes.data_as(ctypes.c_void_p),
+                               res.ctypes.data_as(ctypes.c_void_p)))
+    if t < 0:
+        raise ValueError("bulk_find: the forest has a cycle")
+    return out, res, t

@@ -146,6 +146,37 @@ int64_t oracle_relabel(oracle_uf* u, const int32_t* edges, int64_t k, int32_t* o
     return m;
 }
 
+/* Bulk-Find (Algorithm 4) on a given forest, by what it leaves behind: every
+ * node on a path from a query node to its root (the union of the traversal
+ * paths of Phase I), other than the root, points at that root afterwards
+ * (Phase II); nothing else changes, and res[i] is the root of S[i]. The same
+ * forest results from serial finds with full path compression in any order,
+ * which is the equivalence of Section 4.2. Walks stop where an earlier walk
+ * already passed (a flow meeting a visited node stops). `parent_in` must be
+ * acyclic; a walk longer than n steps returns -1. Returns the number of
+ * traversed non-root nodes, i.e. |R_u| without R_0. */
+int64_t oracle_bulk_find(int64_t n, const int32_t* parent_in, const int32_t* S, int64_t k,
+                         int32_t* parent_out, int32_t* res) {
+    uint8_t* seen = (uint8_t*)calloc((size_t)n, 1);
+    memcpy(parent_out, parent_in, (size_t)n * sizeof(int32_t));
+    int64_t traversed = 0;
+    for (int64_t i = 0; i < k; i++) {
+        int32_t r = S[i];
+        for (int64_t steps = 0; parent_in[r] != r; steps++) {
+            if (steps > n) { free(seen); return -1; }
+            r = parent_in[r];
+        }
+        res[i] = r;
+        for (int32_t x = S[i]; x != r && !seen[x]; x = parent_in[x]) {
+            seen[x] = 1;
+            parent_out[x] = r;
+            traversed++;
+        }
+    }
+    free(seen);
+    return traversed;
+}
+
 int64_t oracle_n(const oracle_uf* u) { return u->n; }
 int64_t oracle_unions(const oracle_uf* u) { return u->unions; }
 int64_t oracle_errors(const oracle_uf* u) { return u->errors; }

@@ -26,7 +26,8 @@ OPTIONS = {"block": OPT_BLOCK, "edges_per_thread": OPT_EDGES_PER_THREAD,
            "query_halving": OPT_QUERY_HALVING, "profile": OPT_PROFILE,
            "update_variant": OPT_UPDATE_VARIANT, "l2_persist": OPT_L2_PERSIST,
            "seg_block": 8, "seg_edges_per_thread": 9, "seg_smem_cap": 10, "seg_graph": 11,
-           "seg_max_ctas": 12, "update_schedule": 13, "link": 14}
+           "seg_max_ctas": 12, "update_schedule": 13, "link": 14,
+           "bulk_find": 15}
 OP_UPDATE, OP_QUERY = 0, 1
 # Layout of cc_op (include/cc.h): graph, kind, data pointer, k, out pointer.
 OP_DTYPE = np.dtype([("graph", "<i4"), ("kind", "<i4"), ("data", "<u8"), ("k", "<i8"),
@@ -89,6 +90,10 @@ def load(path: str | Path | None = None) -> ctypes.CDLL:
         "cc_schedule_stats": [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)],
         "cc_copy_nonloop": [vp, vp, i64, ctypes.POINTER(ctypes.c_int64)],
         "cc_forest_depth": [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)],
+        "cc_bulk_find": [vp, vp, i64, vp],
+        "cc_bulk_find_stats": [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                               ctypes.POINTER(ctypes.c_int32)],
+        "cc_load_forest": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -241,6 +246,28 @@ class Forest:
         v = ctypes.c_int64()
         check(self._L.cc_components(self._h, ctypes.byref(v)), self._L)
         return v.value
+
+    def bulk_find(self, S: torch.Tensor, res: torch.Tensor | None = None) -> torch.Tensor:
+        """Bulk-Find (Algorithm 4): roots of the int32 vertices S, compressing
+        every path walked."""
+        if not S.is_cuda or S.dtype != torch.int32 or not S.is_contiguous():
+            raise TypeError("S: expected a contiguous CUDA int32 tensor")
+        if res is None:
+            res = torch.empty(S.numel(), dtype=torch.int32, device=S.device)
+        check(self._L.cc_bulk_find(self._h, S.data_ptr(), S.numel(), res.data_ptr()), self._L)
+        return res
+
+    def bulk_find_stats(self) -> tuple[int, int, int]:
+        """(traversed non-root vertices, Phase I levels, Phase II levels)."""
+        t, u, d = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        check(self._L.cc_bulk_find_stats(self._h, ctypes.byref(t), ctypes.byref(u), ctypes.byref(d)),
+              self._L)
+        return t.value, u.value, d.value
+
+    def load_forest(self, parent: torch.Tensor) -> None:
+        if parent.dtype != torch.int32 or not parent.is_contiguous() or parent.numel() != self.n:
+            raise TypeError("parent: expected a contiguous int32 tensor of n elements")
+        check(self._L.cc_load_forest(self._h, parent.data_ptr()), self._L)
 
     def depth(self) -> tuple[int, float]:
         """(max, mean) distance from a vertex to its root."""

@@ -51,7 +51,7 @@ struct DeviceScope {
 };
 
 const int64_t kDefaults[CC_OPT__COUNT] = {256, 2, 1, CC_COMPRESS_ALL, 0, 0, 0, 0,
-                                          512, 1, 65536, 1, 0, 0, 0};
+                                          512, 1, 65536, 1, 0, 0, 0, 0};
 
 }  // namespace
 
@@ -98,6 +98,9 @@ struct cc_ctx {
     int* size = nullptr;                 // tree sizes, meaningful at roots
     unsigned long long* best = nullptr;  // per-component vote of the join step
     bool fresh = true;                   // no edge since create / reset
+
+    // Bulk-Find (CC_OPT_BULK_FIND, cc_bulk_find)
+    cc::BulkFindState bf;
 };
 
 namespace {
@@ -204,9 +207,27 @@ cc_status paper_update(cc_ctx* c, const int32_t* edges, int64_t k) {
         c->a2_cap = k;
     }
     const int block = (int)c->opt[CC_OPT_BLOCK];
+    if (c->opt[CC_OPT_BULK_FIND] == 1) {  // relabel with one Bulk-Find over all 2k endpoints
+        const uint64_t before = c->bf.launches;
+        int64_t cres = c->bf.cap_res;
+        if (2 * k > cres) {
+            int* q = nullptr;
+            e = cudaMalloc(&q, sizeof(int) * 2 * (size_t)k);
+            if (e != cudaSuccess) { cudaGetLastError(); return fail(CC_ERR_OOM, "schedule 1: root buffer"); }
+            cudaFree(c->bf.res);
+            c->bf.res = q;
+            c->bf.cap_res = 2 * k;
+        }
+        e = cc::bulk_find(c->bf, c->parent, (int)c->n, edges, 2 * k, c->bf.res, c->ds, c->stream);
+        c->launches[CC_K_UPDATE] += c->bf.launches - before;
+        if (e != cudaSuccess) return cuda_fail(e, "schedule 1: Bulk-Find relabel");
+    }
     cc_status st = run(c, CC_K_UPDATE, "schedule 1: relabel", [&]() -> cudaError_t {
         cudaError_t e1 = cudaMemsetAsync(c->pcount, 0, 2 * sizeof(unsigned), c->stream);
         if (e1 != cudaSuccess) return e1;
+        if (c->opt[CC_OPT_BULK_FIND] == 1)
+            return cc::launch_filter_roots(c->bf.res, k, c->a2, c->pcount, c->comp,
+                                           c->opt[CC_OPT_LINK] == 1 ? c->best : nullptr, block, c->stream);
         if (c->opt[CC_OPT_LINK] == 1)
             return cc::launch_relabel_generic(c->parent, (int)c->n, edges, k, c->a2, c->pcount, c->comp,
                                               c->best, c->ds, block, c->stream);
@@ -353,6 +374,7 @@ cc_status cc_destroy(cc_ctx* c) {
         cudaFree(c->pcount);
         cudaFree(c->size);
         cudaFree(c->best);
+        cc::bulk_find_free(c->bf);
         cudaFree(c->parent);
         cudaFree(c->ds);
     }
@@ -436,6 +458,14 @@ cc_status cc_bulk_query(cc_ctx* c, const int32_t* pairs, int64_t k, uint8_t* out
     if (k > 0 && !out) return fail(CC_ERR_ARG, "cc_bulk_query: out is null");
     if (k == 0) return CC_OK;
     CC_DEVICE(c);
+    if (c->opt[CC_OPT_BULK_FIND] == 1) {
+        const uint64_t before = c->bf.launches;
+        s = run(c, CC_K_QUERY, "bulk_query(Bulk-Find)", [&] {
+            return cc::bulk_find_query(c->bf, c->parent, (int)c->n, pairs, k, out, c->ds, c->stream);
+        });
+        c->launches[CC_K_QUERY] += c->bf.launches - before - 1;  // run() counted one
+        return s;
+    }
     if (by_size(c)) {
         const bool flat = c->flat;
         s = run(c, CC_K_QUERY, "bulk_query(generic)", [&] {
@@ -791,6 +821,9 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
         case CC_OPT_SEG_MAX_CTAS:
             if (value < 0 || value > (1 << 20)) return fail(CC_ERR_ARG, "seg max ctas %lld out of range", (long long)value);
             break;
+        case CC_OPT_BULK_FIND:
+            if (value != 0 && value != 1) return fail(CC_ERR_ARG, "option %d takes 0 or 1", option);
+            break;
         case CC_OPT_LINK: {
             if (value != 0 && value != 1) return fail(CC_ERR_ARG, "link %lld: need 0 (index) or 1 (size)", (long long)value);
             if (value == c->opt[CC_OPT_LINK]) break;
@@ -888,6 +921,54 @@ cc_status cc_copy_nonloop(cc_ctx* c, int32_t* out, int64_t cap, int64_t* count) 
     cudaError_t e = cudaMemcpyAsync(out, c->a2, sizeof(int) * 2 * (size_t)m, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cc_copy_nonloop");
+    return CC_OK;
+}
+
+cc_status cc_bulk_find(cc_ctx* c, const int32_t* S, int64_t k, int32_t* res) {
+    CC_CHECK_CTX(c);
+    if (k < 0 || k > INT32_MAX) return fail(CC_ERR_ARG, "cc_bulk_find: k out of range");
+    if (k == 0) return CC_OK;
+    if (!S || !res) return fail(CC_ERR_ARG, "cc_bulk_find: null array");
+    if (reinterpret_cast<uintptr_t>(S) % 4 || reinterpret_cast<uintptr_t>(res) % 4)
+        return fail(CC_ERR_ARG, "cc_bulk_find: arrays must be 4-byte aligned");
+    CC_DEVICE(c);
+    const uint64_t before = c->bf.launches;
+    cudaError_t e = cc::bulk_find(c->bf, c->parent, (int)c->n, S, k, res, c->ds, c->stream);
+    c->launches[CC_K_QUERY] += c->bf.launches - before;
+    if (e != cudaSuccess) return cuda_fail(e, "cc_bulk_find");
+    return CC_OK;
+}
+
+cc_status cc_bulk_find_stats(cc_ctx* c, int64_t* traversed, int32_t* levels_up, int32_t* levels_down) {
+    CC_CHECK_CTX(c);
+    if (traversed) *traversed = c->bf.traversed;
+    if (levels_up) *levels_up = c->bf.levels_up;
+    if (levels_down) *levels_down = c->bf.levels_down;
+    return CC_OK;
+}
+
+cc_status cc_load_forest(cc_ctx* c, const int32_t* parent) {
+    CC_CHECK_CTX(c);
+    if (!parent || reinterpret_cast<uintptr_t>(parent) % 4) return fail(CC_ERR_ARG, "cc_load_forest: null or misaligned");
+    if (c->G > 1 || by_size(c)) return fail(CC_ERR_UNSUPPORTED, "cc_load_forest needs the default link rule on a plain handle");
+    CC_DEVICE(c);
+    cudaError_t e = cudaMemsetAsync(&c->ds->labels_bad, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&c->ds->roots, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = cc::launch_validate_forest(parent, c->n, c->ds, 256, c->stream);
+    cc::DevState h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, c->ds, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cc_load_forest: validate");
+    c->launches[CC_K_LOAD]++;
+    if (h.labels_bad) return fail(CC_ERR_LABELS, "cc_load_forest: need 0 <= parent[v] <= v");
+    unsigned long long unions = (unsigned long long)c->n - h.roots;
+    e = cudaMemcpyAsync(c->parent, parent, sizeof(int) * (size_t)c->n, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&c->ds->unions, &unions, sizeof unions, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cc_load_forest: copy");
+    c->flat = false;
+    c->fresh = false;
+    c->update_calls = 0;
     return CC_OK;
 }
 

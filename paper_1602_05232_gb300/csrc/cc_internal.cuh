@@ -122,6 +122,56 @@ cudaError_t launch_compress_generic(int* parent, int64_t n, int* labels_out, int
 cudaError_t launch_depth(const int* parent, int64_t n, unsigned* max_depth,
                          unsigned long long* sum_depth, DevState* ds, cudaStream_t s);
 
+// ---- Bulk-Find (Algorithm 4) with the Response Distributor ----
+
+struct BulkFindState {
+    int* mark = nullptr;         // n entries: epoch stamp = visited in this call
+    int epoch = 0;
+    int* front[2] = {nullptr, nullptr};
+    int* roots = nullptr;
+    int* D[2] = {nullptr, nullptr};  // Phase II frontiers of (v, root) pairs
+    int64_t cap_front = 0;           // entries of front/roots, pairs of D
+    int* R = nullptr;                // R_u: (from, to) pairs
+    int64_t cap_R = 0;
+    int* sorted = nullptr;           // R_u sorted by bucket
+    int64_t cap_R2 = 0;
+    int* bucket = nullptr;           // rho + 1 bucket offsets
+    int* cursor = nullptr;
+    int64_t cap_bucket = 0;
+    int* scan = nullptr;
+    int64_t cap_scan = 0;
+    int* work = nullptr;             // Phase II: bucket sizes, then their prefix sums
+    int64_t cap_work = 0;
+    int* res = nullptr;              // roots of the query endpoints (Bulk-Query)
+    int64_t cap_res = 0;
+    unsigned* count = nullptr;
+    // statistics of the last call
+    int64_t traversed = 0;           // |R_u| without R_0
+    int32_t levels_up = 0, levels_down = 0;
+    uint64_t launches = 0;           // kernels launched, cumulative
+};
+
+// res[i] = root of S[i] (-1 for an id outside [0, n)); every node on the
+// paths from S to the roots points at its root afterwards. Synchronises once
+// per level.
+cudaError_t bulk_find(BulkFindState& b, int* parent, int n, const int* S, int64_t k, int* res,
+                      DevState* ds, cudaStream_t s);
+// Bulk-Query through one Bulk-Find over all 2k endpoints.
+cudaError_t bulk_find_query(BulkFindState& b, int* parent, int n, const int* pairs, int64_t k,
+                            uint8_t* out, DevState* ds, cudaStream_t s);
+void bulk_find_free(BulkFindState& b);
+// In-place exclusive scan of len ints; scratch needs scan_scratch_ints(len) ints.
+int64_t scan_scratch_ints(int64_t len);
+cudaError_t exclusive_scan(int* a, int64_t len, int* scratch, cudaStream_t s);
+
+// A'' from the roots found by a Bulk-Find over the 2k endpoints (res): the
+// pairs whose roots differ, with their component entries initialised.
+cudaError_t launch_filter_roots(const int* res, int64_t k, int* a2, unsigned* m2, int* comp,
+                                unsigned long long* best, int block, cudaStream_t s);
+
+// Checks 0 <= p[v] <= v (and no more); counts roots.
+cudaError_t launch_validate_forest(const int* p, int64_t n, DevState* ds, int block, cudaStream_t s);
+
 // Checks 0 <= lab[v] <= v and lab[lab[v]] == lab[v]; counts roots.
 cudaError_t launch_validate_labels(const int* lab, int64_t n, DevState* ds, int block,
                                    cudaStream_t s);

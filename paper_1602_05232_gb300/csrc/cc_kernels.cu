@@ -432,6 +432,24 @@ k_validate_labels(const int* __restrict__ lab, int64_t n, DevState* __restrict__
     if ((threadIdx.x & 31) == 0 && root) atomicAdd(&ds->roots, (unsigned long long)root);
 }
 
+__global__ void __launch_bounds__(1024)
+k_validate_forest(const int* __restrict__ p, int64_t n, DevState* __restrict__ ds) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int root = 0;
+    if (v < n) {
+        const int x = p[v];
+        if (x < 0 || (int64_t)x > v) atomicOr(&ds->labels_bad, 1u);
+        root = (int64_t)x == v;
+    }
+    root = __reduce_add_sync(0xffffffffu, root);
+    if ((threadIdx.x & 31) == 0 && root) atomicAdd(&ds->roots, (unsigned long long)root);
+}
+
+cudaError_t launch_validate_forest(const int* p, int64_t n, DevState* ds, int block, cudaStream_t s) {
+    k_validate_forest<<<blocks_for(n, block), block, 0, s>>>(p, n, ds);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_validate_labels(const int* lab, int64_t n, DevState* ds, int block,
                                    cudaStream_t s) {
     k_validate_labels<<<blocks_for(n, block), block, 0, s>>>(lab, n, ds);

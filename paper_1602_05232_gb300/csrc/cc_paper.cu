@@ -372,6 +372,37 @@ cudaError_t launch_compress_generic(int* parent, int64_t n, int* labels_out, int
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void __launch_bounds__(1024)
+k_filter_roots(const int* __restrict__ res, int64_t k, int* __restrict__ a2, unsigned* __restrict__ m2,
+               int* __restrict__ comp, unsigned long long* __restrict__ best) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool has = false;
+    int ru = 0, rv = 0;
+    if (i < k) {
+        ru = res[2 * i];
+        rv = res[2 * i + 1];
+        if (ru >= 0 && rv >= 0 && ru != rv) {
+            has = true;
+            comp[ru] = ru;
+            comp[rv] = rv;
+            if (best) {
+                best[ru] = 0ull;
+                best[rv] = 0ull;
+            }
+        }
+    }
+    append_pair(has, ru, rv, a2, m2);
+}
+}  // namespace
+
+cudaError_t launch_filter_roots(const int* res, int64_t k, int* a2, unsigned* m2, int* comp,
+                                unsigned long long* best, int block, cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    k_filter_roots<<<grid1(k, block), block, 0, s>>>(res, k, a2, m2, comp, best);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_depth(const int* parent, int64_t n, unsigned* max_depth,
                          unsigned long long* sum_depth, DevState* ds, cudaStream_t s) {
     k_depth<<<grid1(n, 256), 256, 0, s>>>(parent, n, max_depth, sum_depth, ds);

@@ -306,8 +306,94 @@ def pin_relabel(lib) -> list[str]:
     return fails
 
 
+def serial_finds(parent, order):
+    """Textbook serial find with full path compression, applied in `order`."""
+    p = list(parent)
+    for s in order:
+        r = s
+        while p[r] != r:
+            r = p[r]
+        x = s
+        while p[x] != r and x != r:
+            nxt = p[x]
+            p[x] = r
+            x = nxt
+    return p
+
+
+def random_forest(rng, n, shape):
+    """Seeded random forest on 0..n-1. 'index': parent[v] <= v (the GPU
+    path's invariant); 'any': parents point anywhere, no cycles."""
+    if shape == "index":
+        par = np.arange(n)
+        for v in range(1, n):
+            if rng.random() < 0.8:
+                par[v] = int(rng.integers(0, v))
+        return par.astype(np.int32)
+    order = rng.permutation(n)
+    par = np.arange(n)
+    for i in range(1, n):
+        if rng.random() < 0.8:
+            par[order[i]] = order[int(rng.integers(0, i))]
+    return par.astype(np.int32)
+
+
+def pin_bulk_find(lib) -> list[str]:
+    """Bulk-Find against the Figure 1 example (golden fixture) and against
+    serial finds with full path compression in several orders, including the
+    dependency order the paper derives (Section 4.2)."""
+    fails = []
+    g = {"parent": [], "expect_parent": []}
+    for line in (GOLDEN / "figure1_bulk_find.txt").read_text().splitlines():
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        key, *vals = line.split()
+        vals = [int(x) for x in vals]
+        if key in ("parent", "expect_parent"):
+            g[key].append(vals)
+        else:
+            g[key] = vals
+    n = g["n"][0]
+    par = np.arange(n, dtype=np.int32)
+    for c, p in g["parent"]:
+        par[c] = p
+    want = par.copy()
+    for c, p in g["expect_parent"]:
+        want[c] = p
+    out, res, t = oracle.bulk_find(par, g["query"], lib=lib)
+    if not np.array_equal(out, want):
+        fails.append("figure 1: forest after Bulk-Find")
+    if res.tolist() != g["expect_res"] or t != g["expect_traversed"][0]:
+        fails.append("figure 1: roots or traversal count")
+    if serial_finds(par.tolist(), g["serial_order"]) != out.tolist():
+        fails.append("figure 1: serial finds in the paper's order")
+    r = _rng(4242)
+    for trial in range(60):
+        n = int(r.integers(2, 80))
+        par = random_forest(r, n, "any" if trial % 2 else "index")
+        S = r.integers(0, n, size=int(r.integers(1, 2 * n))).astype(np.int32)
+        out, res, t = oracle.bulk_find(par, S, lib=lib)
+        for order in (S.tolist(), S[::-1].tolist(), r.permutation(S).tolist()):
+            if serial_finds(par.tolist(), order) != out.tolist():
+                fails.append(f"bulk find vs serial finds, trial {trial}")
+                break
+        roots = []
+        path_nodes = set()
+        for s in S.tolist():
+            x = s
+            while par[x] != x:
+                path_nodes.add(x)
+                x = int(par[x])
+            roots.append(x)
+        if res.tolist() != roots or t != len(path_nodes):
+            fails.append(f"bulk find roots / traversal count, trial {trial}")
+    return fails
+
+
 ALL_PINS = [pin_bfs_tiny, pin_scipy, pin_star, pin_closed_forms,
-            pin_order_independence, pin_invariants, pin_range_rule, pin_relabel]
+            pin_order_independence, pin_invariants, pin_range_rule, pin_relabel,
+            pin_bulk_find]
 
 
 def run_all(lib) -> list[str]:

@@ -50,6 +50,10 @@ MUTANTS = [
      "if (lab[a] == lab[b]) continue;", "if (lab[a] == lab[b] && a < 0) continue;"),
     ("relabel writes the endpoint instead of its identifier",
      "out[2 * m + 1] = lab[b];", "out[2 * m + 1] = b;"),
+    ("bulk find compresses only the query node",
+     "seen[x] = 1;\n            parent_out[x] = r;", "seen[x] = 1;\n            if (x == S[i]) parent_out[x] = r;"),
+    ("bulk find points at the parent instead of the root",
+     "parent_out[x] = r;\n            traversed++;", "parent_out[x] = parent_in[parent_in[x]];\n            traversed++;"),
 ]
 
 
