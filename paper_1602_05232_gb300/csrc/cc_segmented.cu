@@ -102,6 +102,85 @@ __device__ __forceinline__ void seg_query_smem(const unsigned short* sp, int ng,
     if (bad) flag(ds, ST_RANGE);
 }
 
+// The operations [ob, oe) of one graph in shared memory, software-pipelined:
+// an operation is cut into chunks of blockDim * E pairs, and while a chunk is
+// being worked on, every thread already has the loads of its pairs of the
+// NEXT chunk in flight -- the next chunk of the same operation, or the first
+// one of the graph's next operation (its data does not depend on this one's
+// result). A barrier separates consecutive operations only. Returns the
+// number of links made.
+template <int E>
+__device__ __forceinline__ int seg_run_smem(unsigned short* sp, int ng, const SegOp* __restrict__ ops,
+                                            int ob, int oe, DevState* ds) {
+    const int64_t chunk = (int64_t)blockDim.x * E;
+    const int64_t mine = (int64_t)threadIdx.x * E;
+    int made = 0;
+    bool bad = false;
+    int o = ob;
+    int64_t off = 0;
+    // the current operation, field by field
+    const int* data = nullptr;
+    uint8_t* out = nullptr;
+    int64_t k = 0;
+    int kind = 0;
+    int u[E] = {}, v[E] = {};
+    if (o < oe) {
+        data = ops[o].data; out = ops[o].out; k = ops[o].k; kind = ops[o].kind;
+        if (mine < k) load_pairs<E>(data, mine, k, pair_vec_dev(data), u, v);
+    }
+    while (o < oe) {
+        // where the next chunk is, and its loads
+        int o2 = o;
+        int64_t off2 = off + chunk;
+        const int* data2 = data;
+        uint8_t* out2 = out;
+        int64_t k2 = k;
+        int kind2 = kind;
+        if (off2 >= k) {
+            o2 = o + 1;
+            off2 = 0;
+            if (o2 < oe) {
+                data2 = ops[o2].data; out2 = ops[o2].out; k2 = ops[o2].k; kind2 = ops[o2].kind;
+            }
+        }
+        int nu[E] = {}, nv[E] = {};
+        if (o2 < oe && off2 + mine < k2) load_pairs<E>(data2, off2 + mine, k2, pair_vec_dev(data2), nu, nv);
+        // this chunk
+        const int64_t i0 = off + mine;
+        if (kind == CC_OP_UPDATE) {
+#pragma unroll
+            for (int j = 0; j < E; j++) {
+                if (i0 + j >= k) break;
+                if (!(in_range(u[j], ng) && in_range(v[j], ng))) {
+                    bad = true;
+                    continue;
+                }
+                made += shook(sp, sfind(sp, u[j]), sfind(sp, v[j]));
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < E; j++) {
+                if (i0 + j >= k) break;
+                uint8_t a = 0;
+                if (in_range(u[j], ng) && in_range(v[j], ng))
+                    a = (uint8_t)(sroot(sp, u[j]) == sroot(sp, v[j]));
+                else
+                    bad = true;
+                out[i0 + j] = a;
+            }
+        }
+        if (o2 != o) __syncthreads();  // the operation is complete before the next starts
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            u[j] = nu[j];
+            v[j] = nv[j];
+        }
+        o = o2; off = off2; data = data2; out = out2; k = k2; kind = kind2;
+    }
+    if (bad) flag(ds, ST_RANGE);
+    return made;
+}
+
 // --- the same operations in place on the global forest (large graphs) ----
 
 template <int E>
@@ -155,7 +234,7 @@ __device__ __forceinline__ void seg_query_global(int* parent, int64_t base, int 
 }  // namespace
 
 template <int E>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(1024, 1)
 k_segmented(int* __restrict__ parent, const int64_t* __restrict__ seg_off, SegTables t,
             unsigned* __restrict__ queue, DevState* __restrict__ ds, int smem_cap) {
     extern __shared__ unsigned short sp[];
@@ -183,12 +262,7 @@ k_segmented(int* __restrict__ parent, const int64_t* __restrict__ seg_off, SegTa
                 }
             }
             __syncthreads();
-            for (int o = ob; o < oe; o++) {
-                const SegOp op = t.ops[o];
-                if (op.kind == CC_OP_UPDATE) made += seg_update_smem<E>(sp, ng, op, ds);
-                else seg_query_smem<E>(sp, ng, op, ds);
-                __syncthreads();
-            }
+            made += seg_run_smem<E>(sp, ng, t.ops, ob, oe, ds);
             for (int v = threadIdx.x; v < ng; v += blockDim.x)
                 parent[base + v] = (int)(base + sroot(sp, v));
             __syncthreads();  // the slice is out before the buffer is reused
