@@ -259,8 +259,8 @@ cc_status cc_submit(cc_ctx* ctx, const cc_op* ops, int64_t nops);
  *    overlaps a later update.
  * A request is admitted when its footprint (8 bytes in + 1 byte out per
  * pair) fits in the free part of the ring; otherwise it waits for earlier
- * groups to finish. Latency runs from enqueue to the host callback that
- * follows the group's last device operation. */
+ * groups to finish. Latency runs from enqueue to the moment a completion
+ * thread sees the event recorded after the group's last device operation. */
 typedef struct cc_server cc_server;
 
 typedef struct {

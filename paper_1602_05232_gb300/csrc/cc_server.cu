@@ -9,13 +9,14 @@
 //    the device staging ring for each group, copies the group's host data in
 //    on the h2d stream, and launches ONE Bulk-Update or Bulk-Query over the
 //    range on the compute stream (after the copy). Query answers go back on
-//    the d2h stream. A host callback after the group's last operation stamps
-//    the completion time and frees its ring range;
+//    the d2h stream. An event recorded after the group's last operation is
+//    watched by a completion thread, which stamps the completion time and
+//    frees the group's ring range;
 //  - groups compute in arrival order on the single compute stream, so a
 //    query sees exactly the updates that arrived before it. Merging adjacent
 //    updates is exact because the graph is the union of the edge sets.
-// The worker never holds the lock while calling CUDA, and host callbacks only
-// take the lock, so neither can wait on the other.
+// Neither thread holds the lock while it calls CUDA, so neither can wait on
+// the other.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -52,6 +53,8 @@ struct Group {
     cc_server* srv;
     int64_t first, last;  // requests [first, last)
     int64_t b, e;         // ring range [b, e) in pairs
+    cudaEvent_t ev = nullptr;  // recorded after the group's last operation
+    bool launched = false;     // ev has been recorded
     bool done = false;
 };
 
@@ -79,27 +82,74 @@ struct cc_server {
     cc_status err = CC_OK;
     std::string errmsg;
     std::thread worker;
+    std::thread reaper;                 // completion thread
+    std::vector<cudaEvent_t> spare_events;
 };
 
 namespace {
 
-// Called by CUDA after a group's last device operation.
-void CUDART_CB on_group_done(void* arg) {
-    Group* g = static_cast<Group*>(arg);
-    cc_server* s = g->srv;
-    const double t = now_s();
+void fail_worker(cc_server* s, cudaError_t e, const char* what) {
     std::lock_guard<std::mutex> lk(s->mu);
+    if (s->err == CC_OK) {
+        s->err = CC_ERR_CUDA;
+        s->errmsg = std::string(what) + ": " + cudaGetErrorString(e);
+    }
+    s->cv.notify_all();
+}
+
+// A group's work is complete: stamp its requests, free ring ranges in order.
+// Called with the lock held.
+void mark_done(cc_server* s, Group* g, double t) {
     for (int64_t i = g->first; i < g->last; i++) {
         s->reqs[i].t_done = t;
         s->reqs[i].done = true;
     }
     s->completed += g->last - g->first;
     g->done = true;
-    while (!s->inflight.empty() && s->inflight.front()->done) {  // free ring ranges in order
-        delete s->inflight.front();
+    while (!s->inflight.empty() && s->inflight.front()->done) {
+        Group* f = s->inflight.front();
+        s->spare_events.push_back(f->ev);
+        delete f;
         s->inflight.pop_front();
     }
     s->cv.notify_all();
+}
+
+// Completion thread: polls the events of the groups in flight (a dedicated
+// thread keeps the time from completion to notice to a few microseconds).
+void reaper_loop(cc_server* s) {
+    cudaSetDevice(s->device);
+    std::vector<Group*> watch;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv.wait(lk, [&] {
+                if (s->err != CC_OK) return true;
+                for (Group* g : s->inflight)
+                    if (g->launched && !g->done) return true;
+                return s->stop && s->next_launch >= (int64_t)s->reqs.size() && s->inflight.empty();
+            });
+            if (s->err != CC_OK) return;
+            watch.clear();
+            for (Group* g : s->inflight)
+                if (g->launched && !g->done) watch.push_back(g);
+            if (watch.empty()) return;  // stopping, nothing left
+        }
+        bool any = false;
+        for (Group* g : watch) {
+            const cudaError_t q = cudaEventQuery(g->ev);  // no lock held
+            if (q == cudaSuccess) {
+                const double t = now_s();
+                std::lock_guard<std::mutex> lk(s->mu);
+                mark_done(s, g, t);
+                any = true;
+            } else if (q != cudaErrorNotReady) {
+                fail_worker(s, q, "serve: completion");
+                return;
+            }
+        }
+        if (!any) std::this_thread::yield();
+    }
 }
 
 // Reserve [b, b+k) of the ring (FIFO). Called with the lock held.
@@ -125,14 +175,6 @@ bool ring_alloc(cc_server* s, int64_t k, int64_t* b) {
     return false;  // head == tail with work in flight: full
 }
 
-void fail_worker(cc_server* s, cudaError_t e, const char* what) {
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (s->err == CC_OK) {
-        s->err = CC_ERR_CUDA;
-        s->errmsg = std::string(what) + ": " + cudaGetErrorString(e);
-    }
-    s->cv.notify_all();
-}
 
 void worker_loop(cc_server* s) {
     cudaSetDevice(s->device);
@@ -164,6 +206,10 @@ void worker_loop(cc_server* s) {
                 if (s->err != CC_OK) return;
             }
             g = new Group{s, first, last, b, b + total};
+            if (!s->spare_events.empty()) {
+                g->ev = s->spare_events.back();
+                s->spare_events.pop_back();
+            }
             s->inflight.push_back(g);
             s->head = b + total;
             s->next_launch = last;
@@ -178,28 +224,66 @@ void worker_loop(cc_server* s) {
         }
         // --- device work for the group (no lock held) ---
         cudaError_t e = cudaSuccess;
-        for (const Req& r : batch)
-            if (r.k > 0 && e == cudaSuccess)
-                e = cudaMemcpyAsync(s->ring + 2 * r.off, r.data, sizeof(int32_t) * 2 * (size_t)r.k,
+        if (!g->ev) e = cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming);
+        // copy in: one copy per run of requests whose host data is contiguous;
+        // if the driver refuses a run (it spans two separate host
+        // allocations), copy its requests one by one
+        for (size_t i = 0; i < batch.size() && e == cudaSuccess;) {
+            size_t j = i + 1;
+            int64_t pairs = batch[i].k;
+            while (j < batch.size() && batch[j].data == batch[i].data + 2 * pairs) pairs += batch[j++].k;
+            if (pairs > 0) {
+                e = cudaMemcpyAsync(s->ring + 2 * batch[i].off, batch[i].data, sizeof(int32_t) * 2 * (size_t)pairs,
                                     cudaMemcpyHostToDevice, s->h2d);
+                if (e == cudaErrorInvalidValue && j > i + 1) {
+                    cudaGetLastError();
+                    e = cudaSuccess;
+                    for (size_t r = i; r < j && e == cudaSuccess; r++)
+                        if (batch[r].k > 0)
+                            e = cudaMemcpyAsync(s->ring + 2 * batch[r].off, batch[r].data,
+                                                sizeof(int32_t) * 2 * (size_t)batch[r].k, cudaMemcpyHostToDevice, s->h2d);
+                }
+            }
+            i = j;
+        }
         if (e == cudaSuccess) e = cudaEventRecord(s->ev_in, s->h2d);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s->compute, s->ev_in, 0);
         if (e != cudaSuccess) { fail_worker(s, e, "serve: staging copy"); return; }
         if (kind == CC_OP_UPDATE) {
             cc_status st = total ? cc_bulk_update(s->ctx, s->ring + 2 * b, total) : CC_OK;
             if (st != CC_OK) { fail_worker(s, cudaErrorUnknown, "serve: bulk update"); return; }
-            e = cudaLaunchHostFunc(s->compute, on_group_done, g);
+            e = cudaEventRecord(g->ev, s->compute);
         } else {
             cc_status st = total ? cc_bulk_query(s->ctx, s->ring + 2 * b, total, s->ring_out + b) : CC_OK;
             if (st != CC_OK) { fail_worker(s, cudaErrorUnknown, "serve: bulk query"); return; }
             e = cudaEventRecord(s->ev_q, s->compute);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s->d2h, s->ev_q, 0);
-            for (const Req& r : batch)
-                if (r.k > 0 && e == cudaSuccess)
-                    e = cudaMemcpyAsync(r.out, s->ring_out + r.off, (size_t)r.k, cudaMemcpyDeviceToHost, s->d2h);
-            if (e == cudaSuccess) e = cudaLaunchHostFunc(s->d2h, on_group_done, g);
+            for (size_t i = 0; i < batch.size() && e == cudaSuccess;) {  // contiguous outputs: one copy
+                size_t j = i + 1;
+                int64_t pairs = batch[i].k;
+                while (j < batch.size() && batch[j].out == batch[i].out + pairs) pairs += batch[j++].k;
+                if (pairs > 0) {
+                    e = cudaMemcpyAsync(batch[i].out, s->ring_out + batch[i].off, (size_t)pairs,
+                                        cudaMemcpyDeviceToHost, s->d2h);
+                    if (e == cudaErrorInvalidValue && j > i + 1) {  // spans two allocations
+                        cudaGetLastError();
+                        e = cudaSuccess;
+                        for (size_t r = i; r < j && e == cudaSuccess; r++)
+                            if (batch[r].k > 0)
+                                e = cudaMemcpyAsync(batch[r].out, s->ring_out + batch[r].off, (size_t)batch[r].k,
+                                                    cudaMemcpyDeviceToHost, s->d2h);
+                    }
+                }
+                i = j;
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(g->ev, s->d2h);
         }
         if (e != cudaSuccess) { fail_worker(s, e, "serve: launch"); return; }
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            g->launched = true;
+            s->cv.notify_all();
+        }
     }
 }
 
@@ -248,6 +332,7 @@ cc_status cc_server_create(cc_ctx* ctx, const cc_server_config* cfg, cc_server**
     }
     cc_set_stream(ctx, s->compute);
     s->worker = std::thread(worker_loop, s);
+    s->reaper = std::thread(reaper_loop, s);
     *out = s;
     return CC_OK;
 }
@@ -325,6 +410,11 @@ cc_status cc_server_destroy(cc_server* s) {
         s->cv.notify_all();
     }
     if (s->worker.joinable()) s->worker.join();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->cv.notify_all();
+    }
+    if (s->reaper.joinable()) s->reaper.join();
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(s->device);
@@ -332,7 +422,11 @@ cc_status cc_server_destroy(cc_server* s) {
         st = server_fail(CC_ERR_CUDA, "cc_server_destroy: sync");
     cudaStreamSynchronize(s->h2d);
     cc_set_stream(s->ctx, s->prev_stream);
-    for (Group* g : s->inflight) delete g;
+    for (Group* g : s->inflight) {
+        if (g->ev) cudaEventDestroy(g->ev);
+        delete g;
+    }
+    for (cudaEvent_t ev : s->spare_events) cudaEventDestroy(ev);
     cudaFree(s->ring);
     cudaFree(s->ring_out);
     cudaEventDestroy(s->ev_in);
