@@ -291,3 +291,28 @@ def test_paper_scale_random_stream_component_curve(cc):
         assert f.components() == ref.components, f"component count at minibatch {i}"
     assert np.array_equal(f.labels().cpu().numpy(), ref.labels())
     f.sync()
+
+
+def test_single_vertex_forest(cc):
+    f = cc.Forest(1)
+    f.bulk_update(dev(np.array([[0, 0]], dtype=np.int32)))
+    assert f.bulk_query(dev(np.array([[0, 0]], dtype=np.int32))).cpu().tolist() == [1]
+    assert f.labels().cpu().tolist() == [0] and f.components() == 1
+    f.sync()
+
+
+def test_maximum_vertex_count(cc):
+    # n = 2^31 - 1, the largest the int32 ids allow: an 8 GiB forest; edges at
+    # both ends of the id range, checked through answers and component counts
+    n = 2**31 - 1
+    f = cc.Forest(n, **{"compress_every": 1})
+    e = np.array([[n - 1, n - 2], [0, n - 1], [1 << 30, (1 << 30) + 1], [n - 3, n - 3]], dtype=np.int32)
+    f.bulk_update(dev(e))
+    assert f.components() == n - 3
+    q = np.array([[0, n - 2], [n - 2, n - 1], [1, n - 1], [1 << 30, (1 << 30) + 1], [n - 3, n - 3]],
+                 dtype=np.int32)
+    assert f.bulk_query(dev(q)).cpu().tolist() == [1, 1, 0, 1, 1]
+    par = f.parent()
+    assert int(par[n - 1]) == 0 and int(par[n - 2]) == 0
+    f.sync()
+    f.close()
