@@ -77,10 +77,11 @@ typedef enum {
     CC_OPT_UPDATE_VARIANT = 6,   /* Bulk-Update kernel: 0 per-edge walks, 1 lockstep walks of all
                                     endpoints of a thread, 2 = 1 on a persistent grid that prefetches
                                     the next edges (default 0) */
-    CC_OPT_L2_PERSIST = 7,       /* 1: ask L2 to keep the forest resident (an access-policy window
-                                    set on the handle's stream around each kernel; the process's
-                                    persisting-L2 limit is raised to the forest size, capped by the
-                                    device maximum). Best effort; default 0 */
+    CC_OPT_L2_PERSIST = 7,       /* 1: ask L2 to keep the forest resident: the Bulk-Update and
+                                    Bulk-Query kernels are launched with an access-policy window
+                                    over the forest (a per-launch attribute; the stream is not
+                                    changed), and the process's persisting-L2 limit is raised to
+                                    the forest size, capped by the device maximum. Default 0 */
     CC_OPT_SEG_BLOCK = 8,        /* batched form: threads per CTA of the persistent kernel (default 512) */
     CC_OPT_SEG_EDGES_PER_THREAD = 9, /* batched form: edges (pairs) per thread per step: 1, 2, 4 (default 1) */
     CC_OPT_SEG_SMEM_CAP = 10,    /* batched form: graphs of at most this many vertices are processed in
@@ -104,7 +105,10 @@ typedef enum {
                                     find all their roots with ONE Bulk-Find (Algorithm 4), whose
                                     path compression is shared by the whole minibatch (Theorem 3).
                                     Synchronises once per tree level. Default 0 */
-    CC_OPT__COUNT = 16
+    CC_OPT_QUERY_VARIANT = 16,   /* Bulk-Query kernel: 0 = one chunk of pairs per thread (default),
+                                    1 = a persistent grid that loads the next chunk's pairs while
+                                    working on the current one */
+    CC_OPT__COUNT = 17
 } cc_option;
 
 /* Kernel kinds reported by the launch counters and the profiler. */

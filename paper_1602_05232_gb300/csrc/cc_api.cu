@@ -51,7 +51,7 @@ struct DeviceScope {
 };
 
 const int64_t kDefaults[CC_OPT__COUNT] = {256, 2, 1, CC_COMPRESS_ALL, 0, 0, 0, 0,
-                                          512, 1, 65536, 1, 0, 0, 0, 0};
+                                          512, 1, 65536, 1, 0, 0, 0, 0, 0};
 
 }  // namespace
 
@@ -126,21 +126,8 @@ cc_status run(cc_ctx* c, int kind, const char* what, F&& launch) {
         b = take_event(c);
         if (a && b) cudaEventRecord(a, c->stream);
     }
-    const bool window = c->window.num_bytes > 0;
-    if (window) {
-        cudaStreamAttrValue v = {};
-        v.accessPolicyWindow = c->window;
-        if (cudaStreamSetAttribute(c->stream, cudaStreamAttributeAccessPolicyWindow, &v) != cudaSuccess)
-            cudaGetLastError();  // best effort: e.g. the legacy default stream
-    }
     cudaError_t e = launch();
     c->launches[kind]++;
-    if (window) {
-        cudaStreamAttrValue v = {};
-        v.accessPolicyWindow.num_bytes = 0;
-        if (cudaStreamSetAttribute(c->stream, cudaStreamAttributeAccessPolicyWindow, &v) != cudaSuccess)
-            cudaGetLastError();
-    }
     if (a && b) {
         cudaEventRecord(b, c->stream);
         c->pending.push_back({kind, a, b});
@@ -151,7 +138,8 @@ cc_status run(cc_ctx* c, int kind, const char* what, F&& launch) {
 
 cc::Launch cfg_of(const cc_ctx* c) {
     return cc::Launch{(int)c->opt[CC_OPT_BLOCK], (int)c->opt[CC_OPT_EDGES_PER_THREAD],
-                      (int)c->opt[CC_OPT_UPDATE_VARIANT]};
+                      (int)c->opt[CC_OPT_UPDATE_VARIANT], (int)c->opt[CC_OPT_QUERY_VARIANT],
+                      c->window.num_bytes > 0 ? &c->window : nullptr};
 }
 
 cc_status check_pairs(const int32_t* p, int64_t k, const char* name) {
@@ -821,6 +809,7 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
         case CC_OPT_SEG_MAX_CTAS:
             if (value < 0 || value > (1 << 20)) return fail(CC_ERR_ARG, "seg max ctas %lld out of range", (long long)value);
             break;
+        case CC_OPT_QUERY_VARIANT:
         case CC_OPT_BULK_FIND:
             if (value != 0 && value != 1) return fail(CC_ERR_ARG, "option %d takes 0 or 1", option);
             break;

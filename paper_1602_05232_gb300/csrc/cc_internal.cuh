@@ -29,6 +29,8 @@ struct Launch {
     int block;        // threads per block, multiple of 32
     int ept;          // edges (pairs) per thread: 1, 2 or 4
     int variant = 0;  // update kernel: 0 per-edge walks, 1 lockstep walks, 2 persistent + prefetch
+    int query_variant = 0;  // query kernel: 0 one chunk per thread, 1 persistent + prefetch
+    const cudaAccessPolicyWindow* window = nullptr;  // L2 window over the forest, or none
 };
 
 // Alignment class of a pair array: 2 = 16-byte, 1 = 8-byte, 0 = 4-byte.

@@ -15,6 +15,28 @@ static inline unsigned blocks_for(int64_t work, int64_t per_block) {
     return (unsigned)((work + per_block - 1) / per_block);
 }
 
+// Launch with an optional L2 access-policy window as a per-launch attribute
+// (it applies to this kernel only; the stream is left as it is).
+template <typename... Params, typename... Args>
+static void launch_windowed(void (*kernel)(Params...), unsigned grid, int block, cudaStream_t s,
+                            const cudaAccessPolicyWindow* window, Args... args) {
+    if (!window) {
+        kernel<<<grid, block, 0, s>>>(args...);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[0].val.accessPolicyWindow = *window;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ------------------------------------------------------------------ reset
 
 // parent[v] = v: n singletons, the empty graph G_0.
@@ -151,20 +173,20 @@ static int resident_blocks(int block) {
 
 template <int E, int VARIANT>
 static void update_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
-                        int block, cudaStream_t s) {
+                        int block, const cudaAccessPolicyWindow* window, cudaStream_t s) {
     int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
     if (VARIANT == 2) {
         const int64_t cap = resident_blocks<E, VARIANT>(block);
         if (g > cap) g = cap;
     }
-    k_update<E, VARIANT><<<(unsigned)g, block, 0, s>>>(parent, n, edges, k, vec, ds);
+    launch_windowed(k_update<E, VARIANT>, (unsigned)g, block, s, window, parent, n, edges, k, vec, ds);
 }
 
 cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevState* ds,
                           Launch cfg, cudaStream_t s) {
     if (k <= 0) return cudaSuccess;
     const int vec = pair_vec(edges);
-#define CC_UPD(E, V) update_inst<E, V>(edges, k, vec, parent, n, ds, cfg.block, s)
+#define CC_UPD(E, V) update_inst<E, V>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, s)
     switch (cfg.variant * 8 + cfg.ept) {
         case 1: CC_UPD(1, 0); break;
         case 2: CC_UPD(2, 0); break;
@@ -211,13 +233,9 @@ __device__ __forceinline__ void store_answers(uint8_t* __restrict__ out, int64_t
 //  MODE 1: finds with path halving (they write, so ordinary loads).
 //  MODE 2: flat forest (every tree of height <= 1): parent equality decides.
 template <int E, int MODE>
-__global__ void __launch_bounds__(1024)
-k_query(int* __restrict__ parent, int n, const int* __restrict__ pairs, int64_t k, int vec,
-        uint8_t* __restrict__ out, int ovec, DevState* __restrict__ ds) {
-    const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
-    if (e0 >= k) return;
-    int u[E], v[E];
-    load_pairs<E>(pairs, e0, k, vec, u, v);
+__device__ __forceinline__ bool query_chunk(int* __restrict__ parent, int n, int (&u)[E], int (&v)[E],
+                                            int64_t e0, int64_t k, uint8_t (&a)[E],
+                                            DevState* __restrict__ ds) {
     bool ok[E];
     bool bad = false;
 #pragma unroll
@@ -230,7 +248,6 @@ k_query(int* __restrict__ parent, int n, const int* __restrict__ pairs, int64_t 
         if (!ok[i]) { u[i] = 0; v[i] = 0; }
     }
     int pu[E], pv[E];
-    uint8_t a[E];
 #pragma unroll
     for (int i = 0; i < E; i++) {
         if (MODE == 1) {
@@ -280,18 +297,80 @@ k_query(int* __restrict__ parent, int n, const int* __restrict__ pairs, int64_t 
             a[i] = (uint8_t)(ok[i] && (pu[i] == pv[i] || x[2 * i] == x[2 * i + 1]));
         }
     }
-    store_answers<E>(out, e0, k, ovec != 0, a);
+    return bad;
+}
+
+// Algorithm 1 over E pairs per thread. Lanes of a warp own consecutive pairs,
+// so the pair loads (16 B per lane) and the answer stores (E bytes per lane)
+// are coalesced across the warp.
+//  MODE 0: read-only finds through the read-only data path; the 2E walks of a
+//          thread advance in lockstep so their loads overlap.
+//  MODE 1: finds with path halving (they write, so ordinary loads).
+//  MODE 2: flat forest (every tree of height <= 1): parent equality decides.
+// PERSIST: a persistent grid that loads the next chunk's pairs before working
+// on the current one, so those loads overlap the parent reads.
+template <int E, int MODE, bool PERSIST>
+__global__ void __launch_bounds__(1024)
+k_query(int* __restrict__ parent, int n, const int* __restrict__ pairs, int64_t k, int vec,
+        uint8_t* __restrict__ out, int ovec, DevState* __restrict__ ds) {
+    int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
+    if (e0 >= k) return;
+    bool bad = false;
+    int u[E], v[E];
+    uint8_t a[E];
+    load_pairs<E>(pairs, e0, k, vec, u, v);
+    if (!PERSIST) {
+        bad = query_chunk<E, MODE>(parent, n, u, v, e0, k, a, ds);
+        store_answers<E>(out, e0, k, ovec != 0, a);
+    } else {
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x * E;
+        while (e0 < k) {
+            const int64_t nx = e0 + stride;
+            int nu[E] = {}, nv[E] = {};
+            if (nx < k) load_pairs<E>(pairs, nx, k, vec, nu, nv);
+            bad |= query_chunk<E, MODE>(parent, n, u, v, e0, k, a, ds);
+            store_answers<E>(out, e0, k, ovec != 0, a);
+#pragma unroll
+            for (int i = 0; i < E; i++) {
+                u[i] = nu[i];
+                v[i] = nv[i];
+            }
+            e0 = nx;
+        }
+    }
     if (bad) flag(ds, ST_RANGE);
+}
+
+template <int E, int MODE, bool PERSIST>
+static void query_one(unsigned g, int block, const cudaAccessPolicyWindow* window, cudaStream_t s,
+                      int* parent, int n, const int* pairs, int64_t k, int vec, uint8_t* out, int ovec,
+                      DevState* ds) {
+    if (PERSIST) {
+        static int cached[33] = {};
+        int& c = cached[block / 32];
+        if (!c) {
+            int per_sm = 0, dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_query<E, MODE, PERSIST>, block, 0);
+            c = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+        }
+        if (g > (unsigned)c) g = (unsigned)c;
+    }
+    launch_windowed(k_query<E, MODE, PERSIST>, g, block, s, window, parent, n, pairs, k, vec, out, ovec, ds);
 }
 
 template <int MODE>
 static void query_inst(unsigned g, Launch cfg, cudaStream_t s, int* parent, int n,
                        const int* pairs, int64_t k, int vec, uint8_t* out, int ovec, DevState* ds) {
+#define CC_Q(E, P) query_one<E, MODE, P>(g, cfg.block, cfg.window, s, parent, n, pairs, k, vec, out, ovec, ds)
+    const bool persist = cfg.query_variant == 1;
     switch (cfg.ept) {
-        case 1: k_query<1, MODE><<<g, cfg.block, 0, s>>>(parent, n, pairs, k, vec, out, ovec, ds); break;
-        case 2: k_query<2, MODE><<<g, cfg.block, 0, s>>>(parent, n, pairs, k, vec, out, ovec, ds); break;
-        default: k_query<4, MODE><<<g, cfg.block, 0, s>>>(parent, n, pairs, k, vec, out, ovec, ds); break;
+        case 1: if (persist) CC_Q(1, true); else CC_Q(1, false); break;
+        case 2: if (persist) CC_Q(2, true); else CC_Q(2, false); break;
+        default: if (persist) CC_Q(4, true); else CC_Q(4, false); break;
     }
+#undef CC_Q
 }
 
 cudaError_t launch_query(int* parent, int n, const int* pairs, int64_t k, uint8_t* out,

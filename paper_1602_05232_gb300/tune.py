@@ -42,9 +42,10 @@ PLAIN_SPACE = {
     "compress_scope": [0, 1],
     "query_halving": [0, 1],
     "l2_persist": [0, 1],
+    "query_variant": [0, 1],
 }
 PLAIN_START = {"update_variant": 0, "edges_per_thread": 2, "block": 256, "compress_every": 1,
-               "compress_scope": 0, "query_halving": 0, "l2_persist": 0}
+               "compress_scope": 0, "query_halving": 0, "l2_persist": 0, "query_variant": 0}
 
 SEG_SPACE = {
     "seg_block": [128, 256, 512, 1024],

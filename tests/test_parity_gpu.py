@@ -31,6 +31,9 @@ OPTION_SETS = {
     "persistent_ept4": {"update_variant": 2, "edges_per_thread": 4},
     "persistent_ept1_b1024": {"update_variant": 2, "edges_per_thread": 1, "block": 1024},
     "l2_persist": {"l2_persist": 1, "update_variant": 2, "edges_per_thread": 2},
+    "persistent_query": {"query_variant": 1, "compress_every": 0, "edges_per_thread": 4},
+    "persistent_query_halving": {"query_variant": 1, "compress_every": 0, "query_halving": 1},
+    "persistent_query_flat": {"query_variant": 1, "compress_every": 1, "block": 1024},
 }
 
 
@@ -86,7 +89,8 @@ def test_uniform_small_every_batch(cc, opts):
 
 
 @pytest.mark.parametrize("opts", ["default", "ept1_b64", "no_compress", "touched_compress",
-                                  "lockstep_ept4_nocompress", "persistent_ept4"])
+                                  "lockstep_ept4_nocompress", "persistent_ept4",
+                                  "persistent_query_halving"])
 def test_rmat_small(cc, opts):
     s = I.rmat_stream(scale=16, m=1 << 20, batch=(1 << 16) + 3, q=(1 << 16) - 5, seed=1)
     run_stream(cc, s, OPTION_SETS[opts], label_every=4, check_invariants=True)
