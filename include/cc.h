@@ -72,7 +72,10 @@ typedef enum {
     CC_OPT_EDGES_PER_THREAD = 1, /* edges (or pairs) per thread in update and query: 1, 2 or 4 (default 2) */
     CC_OPT_COMPRESS_EVERY = 2,   /* cc_bulk_update compresses after every c-th call; 0 = never (default 1) */
     CC_OPT_COMPRESS_SCOPE = 3,   /* scope of that automatic compression: a cc_compress_scope (default ALL) */
-    CC_OPT_QUERY_HALVING = 4,    /* 1: Bulk-Query finds also halve paths (they write); 0: read-only finds (default) */
+    CC_OPT_QUERY_HALVING = 4,    /* how Bulk-Query finds walk: 0 read-only, all walks of a thread in
+                                    lockstep (default); 1 path halving, one pair after the other;
+                                    2 path splitting, all walks in lockstep (1 and 2 write, which
+                                    shortens paths for later operations) */
     CC_OPT_PROFILE = 5,          /* 1: time every kernel with CUDA events on the handle's stream */
     CC_OPT_UPDATE_VARIANT = 6,   /* Bulk-Update kernel: 0 per-edge walks, 1 lockstep walks of all
                                     endpoints of a thread, 2 = 1 on a persistent grid that prefetches

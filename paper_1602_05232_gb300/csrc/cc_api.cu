@@ -463,11 +463,11 @@ cc_status cc_bulk_query(cc_ctx* c, const int32_t* pairs, int64_t k, uint8_t* out
         if (s == CC_OK && !flat) c->flat = false;
         return s;
     }
-    const int mode = c->flat ? 2 : (c->opt[CC_OPT_QUERY_HALVING] ? 1 : 0);
+    const int64_t qh = c->opt[CC_OPT_QUERY_HALVING];
+    const int mode = c->flat ? 2 : (qh == 2 ? 3 : qh == 1 ? 1 : 0);
     s = run(c, CC_K_QUERY, "bulk_query", [&] {
         return cc::launch_query(c->parent, (int)c->n, pairs, k, out, c->ds, mode, cfg_of(c), c->stream);
     });
-    if (s == CC_OK && mode == 1) c->flat = false;
     return s;
 }
 
@@ -791,6 +791,8 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
             if (value != CC_COMPRESS_ALL && value != CC_COMPRESS_TOUCHED) return fail(CC_ERR_ARG, "unknown compress scope");
             break;
         case CC_OPT_QUERY_HALVING:
+            if (value < 0 || value > 2) return fail(CC_ERR_ARG, "query halving %lld: need 0, 1 or 2", (long long)value);
+            break;
         case CC_OPT_PROFILE:
             if (value != 0 && value != 1) return fail(CC_ERR_ARG, "option %d takes 0 or 1", option);
             break;

@@ -50,7 +50,7 @@ cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevSt
                           Launch cfg, cudaStream_t s);
 
 // mode: 0 read-only finds, 1 finds with path halving, 2 flat forest (parent
-// equality decides).
+// equality decides), 3 lockstep finds with path splitting.
 cudaError_t launch_query(int* parent, int n, const int* pairs, int64_t k, uint8_t* out,
                          DevState* ds, int mode, Launch cfg, cudaStream_t s);
 

@@ -225,13 +225,8 @@ __device__ __forceinline__ void store_answers(uint8_t* __restrict__ out, int64_t
         if (e0 + i < k) out[e0 + i] = a[i];
 }
 
-// Algorithm 1 over E pairs per thread. Lanes of a warp own consecutive pairs,
-// so the pair loads (16 B per lane) and the answer stores (E bytes per lane)
-// are coalesced across the warp.
-//  MODE 0: read-only finds through the read-only data path; the 2E walks of a
-//          thread advance in lockstep so their loads overlap.
-//  MODE 1: finds with path halving (they write, so ordinary loads).
-//  MODE 2: flat forest (every tree of height <= 1): parent equality decides.
+// One chunk of Algorithm 1: the E pairs (u, v) of this thread, answers in a.
+// Returns whether a pair had an id outside [0, n). MODE as for k_query.
 template <int E, int MODE>
 __device__ __forceinline__ bool query_chunk(int* __restrict__ parent, int n, int (&u)[E], int (&v)[E],
                                             int64_t e0, int64_t k, uint8_t (&a)[E],
@@ -250,7 +245,7 @@ __device__ __forceinline__ bool query_chunk(int* __restrict__ parent, int n, int
     int pu[E], pv[E];
 #pragma unroll
     for (int i = 0; i < E; i++) {
-        if (MODE == 1) {
+        if (MODE == 1 || MODE == 3) {
             pu[i] = parent[u[i]];
             pv[i] = parent[v[i]];
         } else {
@@ -270,6 +265,19 @@ __device__ __forceinline__ bool query_chunk(int* __restrict__ parent, int n, int
             int rv = pv[i] == v[i] ? v[i] : find_from(parent, v[i], pv[i], ds);
             a[i] = (uint8_t)(ru == rv);
         }
+    } else if (MODE == 3) {
+        // all 2E walks in lockstep with path splitting (they write)
+        int x[2 * E], p[2 * E];
+#pragma unroll
+        for (int i = 0; i < E; i++) {
+            const bool live = ok[i] && pu[i] != pv[i];
+            x[2 * i] = u[i];     p[2 * i] = live ? pu[i] : u[i];
+            x[2 * i + 1] = v[i]; p[2 * i + 1] = live ? pv[i] : v[i];
+        }
+        walk_split<2 * E>(parent, x, p, ds);
+#pragma unroll
+        for (int i = 0; i < E; i++)
+            a[i] = (uint8_t)(ok[i] && (pu[i] == pv[i] || x[2 * i] == x[2 * i + 1]));
     } else {
         // walk state: x = current node, p = its parent; done when p >= x
         int x[2 * E], p[2 * E];
@@ -305,8 +313,10 @@ __device__ __forceinline__ bool query_chunk(int* __restrict__ parent, int n, int
 // are coalesced across the warp.
 //  MODE 0: read-only finds through the read-only data path; the 2E walks of a
 //          thread advance in lockstep so their loads overlap.
-//  MODE 1: finds with path halving (they write, so ordinary loads).
+//  MODE 1: finds with path halving, one pair after the other (they write, so
+//          ordinary loads).
 //  MODE 2: flat forest (every tree of height <= 1): parent equality decides.
+//  MODE 3: the 2E walks in lockstep with path splitting (they write).
 // PERSIST: a persistent grid that loads the next chunk's pairs before working
 // on the current one, so those loads overlap the parent reads.
 template <int E, int MODE, bool PERSIST>
@@ -381,6 +391,7 @@ cudaError_t launch_query(int* parent, int n, const int* pairs, int64_t k, uint8_
     const unsigned g = blocks_for(k, (int64_t)cfg.ept * cfg.block);
     if (mode == 2) query_inst<2>(g, cfg, s, parent, n, pairs, k, vec, out, ovec, ds);
     else if (mode == 1) query_inst<1>(g, cfg, s, parent, n, pairs, k, vec, out, ovec, ds);
+    else if (mode == 3) query_inst<3>(g, cfg, s, parent, n, pairs, k, vec, out, ovec, ds);
     else query_inst<0>(g, cfg, s, parent, n, pairs, k, vec, out, ovec, ds);
     return cudaGetLastError();
 }

@@ -40,7 +40,7 @@ PLAIN_SPACE = {
     "block": [128, 256, 512, 1024],
     "compress_every": [0, 1, 2, 4, 8, 16],
     "compress_scope": [0, 1],
-    "query_halving": [0, 1],
+    "query_halving": [0, 1, 2],
     "l2_persist": [0, 1],
     "query_variant": [0, 1],
 }
