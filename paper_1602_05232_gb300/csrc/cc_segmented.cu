@@ -45,6 +45,40 @@ __device__ __forceinline__ int sroot(const volatile unsigned short* sp, int x) {
     return x;
 }
 
+// Roots of a and b, walked in lockstep with path splitting (every visited
+// node is repointed at its grandparent): the two chains of dependent
+// shared-memory loads are in flight together instead of one after the other.
+__device__ __forceinline__ void sfind_pair(volatile unsigned short* sp, int& a, int& b) {
+    int pa = sp[a], pb = sp[b];
+    while (pa != a || pb != b) {
+        const int ga = sp[pa], gb = sp[pb];  // both loads issued before either is used
+        if (pa != a) {
+            if (ga != pa) sp[a] = (unsigned short)ga;
+            a = pa;
+            pa = ga;
+        }
+        if (pb != b) {
+            if (gb != pb) sp[b] = (unsigned short)gb;
+            b = pb;
+            pb = gb;
+        }
+    }
+}
+
+// Whether a and b have the same root, in a forest that does not change
+// meanwhile (a Bulk-Query between barriers): both walks in lockstep, stopping
+// early when they meet.
+__device__ __forceinline__ bool ssame(const unsigned short* sp, int a, int b) {
+    int pa = sp[a], pb = sp[b];
+    while (a != b && (pa < a || pb < b)) {
+        a = pa;
+        b = pb;
+        pa = sp[a];
+        pb = sp[b];
+    }
+    return a == b;
+}
+
 __device__ __forceinline__ int shook(unsigned short* sp, int ru, int rv) {
     while (ru != rv) {
         const int hi = ru > rv ? ru : rv;
@@ -55,51 +89,6 @@ __device__ __forceinline__ int shook(unsigned short* sp, int ru, int rv) {
         if (hi == ru) ru = r; else rv = r;
     }
     return 0;
-}
-
-template <int E>
-__device__ __forceinline__ int seg_update_smem(unsigned short* sp, int ng, const SegOp& op,
-                                               DevState* ds) {
-    const int vec = pair_vec_dev(op.data);
-    int made = 0;
-    bool bad = false;
-    for (int64_t i = (int64_t)threadIdx.x * E; i < op.k; i += (int64_t)blockDim.x * E) {
-        int u[E], v[E];
-        load_pairs<E>(op.data, i, op.k, vec, u, v);
-#pragma unroll
-        for (int j = 0; j < E; j++) {
-            if (i + j >= op.k) break;
-            if (!(in_range(u[j], ng) && in_range(v[j], ng))) {
-                bad = true;
-                continue;
-            }
-            made += shook(sp, sfind(sp, u[j]), sfind(sp, v[j]));
-        }
-    }
-    if (bad) flag(ds, ST_RANGE);
-    return made;
-}
-
-template <int E>
-__device__ __forceinline__ void seg_query_smem(const unsigned short* sp, int ng, const SegOp& op,
-                                               DevState* ds) {
-    const int vec = pair_vec_dev(op.data);
-    bool bad = false;
-    for (int64_t i = (int64_t)threadIdx.x * E; i < op.k; i += (int64_t)blockDim.x * E) {
-        int u[E], v[E];
-        load_pairs<E>(op.data, i, op.k, vec, u, v);
-#pragma unroll
-        for (int j = 0; j < E; j++) {
-            if (i + j >= op.k) break;
-            uint8_t a = 0;
-            if (in_range(u[j], ng) && in_range(v[j], ng))
-                a = (uint8_t)(sroot(sp, u[j]) == sroot(sp, v[j]));
-            else
-                bad = true;
-            op.out[i + j] = a;
-        }
-    }
-    if (bad) flag(ds, ST_RANGE);
 }
 
 // The operations [ob, oe) of one graph in shared memory, software-pipelined:
@@ -155,7 +144,9 @@ __device__ __forceinline__ int seg_run_smem(unsigned short* sp, int ng, const Se
                     bad = true;
                     continue;
                 }
-                made += shook(sp, sfind(sp, u[j]), sfind(sp, v[j]));
+                int ru = u[j], rv = v[j];
+                sfind_pair(sp, ru, rv);
+                made += shook(sp, ru, rv);
             }
         } else {
 #pragma unroll
@@ -163,7 +154,7 @@ __device__ __forceinline__ int seg_run_smem(unsigned short* sp, int ng, const Se
                 if (i0 + j >= k) break;
                 uint8_t a = 0;
                 if (in_range(u[j], ng) && in_range(v[j], ng))
-                    a = (uint8_t)(sroot(sp, u[j]) == sroot(sp, v[j]));
+                    a = (uint8_t)ssame(sp, u[j], v[j]);
                 else
                     bad = true;
                 out[i0 + j] = a;
@@ -252,7 +243,24 @@ k_segmented(int* __restrict__ parent, const int64_t* __restrict__ seg_off, SegTa
         const int ng = (int)(seg_off[g + 1] - base);
         const int ob = t.op_begin[g], oe = t.op_begin[g + 1];
         if (ng <= smem_cap) {
-            for (int v = threadIdx.x; v < ng; v += blockDim.x) {
+            // four loads in flight per thread, then the tail one at a time
+            int v = threadIdx.x;
+            for (; v + 3 * (int)blockDim.x < ng; v += 4 * blockDim.x) {
+                int pv[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) pv[j] = __ldcs(parent + base + v + j * blockDim.x);
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int w = v + j * blockDim.x;
+                    int64_t l = (int64_t)pv[j] - base;
+                    if (l < 0 || l > w) {  // not a forest of this slice: keep w alone
+                        flag(ds, ST_CORRUPT);
+                        l = w;
+                    }
+                    sp[w] = (unsigned short)l;
+                }
+            }
+            for (; v < ng; v += blockDim.x) {
                 const int64_t pv = (int64_t)parent[base + v] - base;
                 if (pv < 0 || pv > v) {  // not a forest of this slice: keep v alone
                     flag(ds, ST_CORRUPT);
