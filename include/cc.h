@@ -111,7 +111,14 @@ typedef enum {
     CC_OPT_QUERY_VARIANT = 16,   /* Bulk-Query kernel: 0 = one chunk of pairs per thread (default),
                                     1 = a persistent grid that loads the next chunk's pairs while
                                     working on the current one */
-    CC_OPT__COUNT = 17
+    CC_OPT_PDL = 17,             /* programmatic dependent launch of the Bulk-Update and Bulk-Query
+                                    kernels: 0 = off; 1 = each may become resident while the kernel
+                                    before it on the stream drains, and waits for that kernel to
+                                    complete before it reads anything (results unchanged; default);
+                                    2 = as 1, but each thread's first pairs are read BEFORE that
+                                    wait -- only for pair arrays that the kernel launched just
+                                    before on the same stream does not write */
+    CC_OPT__COUNT = 18
 } cc_option;
 
 /* Kernel kinds reported by the launch counters and the profiler. */

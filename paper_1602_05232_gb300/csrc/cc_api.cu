@@ -51,7 +51,7 @@ struct DeviceScope {
 };
 
 const int64_t kDefaults[CC_OPT__COUNT] = {256, 2, 1, CC_COMPRESS_ALL, 0, 0, 0, 0,
-                                          512, 1, 65536, 1, 0, 0, 0, 0, 0};
+                                          512, 1, 65536, 1, 0, 0, 0, 0, 0, 1};
 
 }  // namespace
 
@@ -139,7 +139,7 @@ cc_status run(cc_ctx* c, int kind, const char* what, F&& launch) {
 cc::Launch cfg_of(const cc_ctx* c) {
     return cc::Launch{(int)c->opt[CC_OPT_BLOCK], (int)c->opt[CC_OPT_EDGES_PER_THREAD],
                       (int)c->opt[CC_OPT_UPDATE_VARIANT], (int)c->opt[CC_OPT_QUERY_VARIANT],
-                      c->window.num_bytes > 0 ? &c->window : nullptr};
+                      c->window.num_bytes > 0 ? &c->window : nullptr, (int)c->opt[CC_OPT_PDL]};
 }
 
 cc_status check_pairs(const int32_t* p, int64_t k, const char* name) {
@@ -792,6 +792,9 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
             break;
         case CC_OPT_QUERY_HALVING:
             if (value < 0 || value > 2) return fail(CC_ERR_ARG, "query halving %lld: need 0, 1 or 2", (long long)value);
+            break;
+        case CC_OPT_PDL:
+            if (value < 0 || value > 2) return fail(CC_ERR_ARG, "pdl %lld: need 0, 1 or 2", (long long)value);
             break;
         case CC_OPT_PROFILE:
             if (value != 0 && value != 1) return fail(CC_ERR_ARG, "option %d takes 0 or 1", option);

@@ -31,6 +31,7 @@ struct Launch {
     int variant = 0;  // update kernel: 0 per-edge walks, 1 lockstep walks, 2 persistent + prefetch
     int query_variant = 0;  // query kernel: 0 one chunk per thread, 1 persistent + prefetch
     const cudaAccessPolicyWindow* window = nullptr;  // L2 window over the forest, or none
+    int pdl = 0;  // programmatic dependent launch: 0 off, 1 wait first, 2 first pairs before the wait
 };
 
 // Alignment class of a pair array: 2 = 16-byte, 1 = 8-byte, 0 = 4-byte.

@@ -15,12 +15,15 @@ static inline unsigned blocks_for(int64_t work, int64_t per_block) {
     return (unsigned)((work + per_block - 1) / per_block);
 }
 
-// Launch with an optional L2 access-policy window as a per-launch attribute
-// (it applies to this kernel only; the stream is left as it is).
+// Launch with per-launch attributes that apply to this kernel only (the
+// stream is left as it is): an optional L2 access-policy window, and
+// programmatic dependent launch, which lets the kernel's CTAs become resident
+// while the kernel before it on the stream drains; the kernel then waits for
+// that one in pdl_wait() (griddepcontrol.wait).
 template <typename... Params, typename... Args>
 static void launch_windowed(void (*kernel)(Params...), unsigned grid, int block, cudaStream_t s,
-                            const cudaAccessPolicyWindow* window, Args... args) {
-    if (!window) {
+                            const cudaAccessPolicyWindow* window, bool pdl, Args... args) {
+    if (!window && !pdl) {
         kernel<<<grid, block, 0, s>>>(args...);
         return;
     }
@@ -29,13 +32,30 @@ static void launch_windowed(void (*kernel)(Params...), unsigned grid, int block,
     cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
-    attr[0].val.accessPolicyWindow = *window;
+    cudaLaunchAttribute attr[2];
+    unsigned na = 0;
+    if (window) {
+        attr[na].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[na].val.accessPolicyWindow = *window;
+        na++;
+    }
+    if (pdl) {
+        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na].val.programmaticStreamSerializationAllowed = 1;
+        na++;
+    }
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = na;
     cudaLaunchKernelEx(&cfg, kernel, args...);
 }
+
+// Programmatic dependent launch, device side. pdl_trigger: the kernel launched
+// after this one on the stream may start placing its CTAs (it still waits in
+// pdl_wait before touching results). pdl_wait: returns once the kernel before
+// this one has completed and its writes are visible; immediately when this
+// kernel was not launched as a dependent.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------ reset
 
@@ -122,16 +142,21 @@ __device__ __forceinline__ int update_edges(int* __restrict__ parent, int n,
     return made;
 }
 
+// early: the first edges are read before the wait for the previous kernel
+// (programmatic dependent launch; see launch_windowed), else after it.
 template <int E, int VARIANT>
 __global__ void __launch_bounds__(1024)
 k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
-         DevState* __restrict__ ds) {
+         DevState* __restrict__ ds, int early) {
+    pdl_trigger();
+    if (!early) pdl_wait();
     int made = 0;
     int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
     if (VARIANT < 2) {
         if (e0 < k) {
             int u[E], v[E];
             load_pairs<E>(edges, e0, k, vec, u, v);
+            if (early) pdl_wait();
             made = update_edges<E, VARIANT>(parent, n, u, v, e0, k, ds);
         }
     } else {
@@ -140,6 +165,7 @@ k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t
         const int64_t stride = (int64_t)gridDim.x * blockDim.x * E;
         int u[E], v[E];
         if (e0 < k) load_pairs<E>(edges, e0, k, vec, u, v);
+        if (early) pdl_wait();
         while (e0 < k) {
             const int64_t nx = e0 + stride;
             int nu[E] = {}, nv[E] = {};
@@ -173,20 +199,21 @@ static int resident_blocks(int block) {
 
 template <int E, int VARIANT>
 static void update_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
-                        int block, const cudaAccessPolicyWindow* window, cudaStream_t s) {
+                        int block, const cudaAccessPolicyWindow* window, int pdl, cudaStream_t s) {
     int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
     if (VARIANT == 2) {
         const int64_t cap = resident_blocks<E, VARIANT>(block);
         if (g > cap) g = cap;
     }
-    launch_windowed(k_update<E, VARIANT>, (unsigned)g, block, s, window, parent, n, edges, k, vec, ds);
+    launch_windowed(k_update<E, VARIANT>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k, vec, ds,
+                    (int)(pdl == 2));
 }
 
 cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevState* ds,
                           Launch cfg, cudaStream_t s) {
     if (k <= 0) return cudaSuccess;
     const int vec = pair_vec(edges);
-#define CC_UPD(E, V) update_inst<E, V>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, s)
+#define CC_UPD(E, V) update_inst<E, V>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, s)
     switch (cfg.variant * 8 + cfg.ept) {
         case 1: CC_UPD(1, 0); break;
         case 2: CC_UPD(2, 0); break;
@@ -319,16 +346,20 @@ __device__ __forceinline__ bool query_chunk(int* __restrict__ parent, int n, int
 //  MODE 3: the 2E walks in lockstep with path splitting (they write).
 // PERSIST: a persistent grid that loads the next chunk's pairs before working
 // on the current one, so those loads overlap the parent reads.
+// early: as for k_update.
 template <int E, int MODE, bool PERSIST>
 __global__ void __launch_bounds__(1024)
 k_query(int* __restrict__ parent, int n, const int* __restrict__ pairs, int64_t k, int vec,
-        uint8_t* __restrict__ out, int ovec, DevState* __restrict__ ds) {
+        uint8_t* __restrict__ out, int ovec, DevState* __restrict__ ds, int early) {
+    pdl_trigger();
+    if (!early) pdl_wait();
     int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
     if (e0 >= k) return;
     bool bad = false;
     int u[E], v[E];
     uint8_t a[E];
     load_pairs<E>(pairs, e0, k, vec, u, v);
+    if (early) pdl_wait();
     if (!PERSIST) {
         bad = query_chunk<E, MODE>(parent, n, u, v, e0, k, a, ds);
         store_answers<E>(out, e0, k, ovec != 0, a);
@@ -352,7 +383,7 @@ k_query(int* __restrict__ parent, int n, const int* __restrict__ pairs, int64_t 
 }
 
 template <int E, int MODE, bool PERSIST>
-static void query_one(unsigned g, int block, const cudaAccessPolicyWindow* window, cudaStream_t s,
+static void query_one(unsigned g, int block, const cudaAccessPolicyWindow* window, int pdl, cudaStream_t s,
                       int* parent, int n, const int* pairs, int64_t k, int vec, uint8_t* out, int ovec,
                       DevState* ds) {
     if (PERSIST) {
@@ -367,13 +398,14 @@ static void query_one(unsigned g, int block, const cudaAccessPolicyWindow* windo
         }
         if (g > (unsigned)c) g = (unsigned)c;
     }
-    launch_windowed(k_query<E, MODE, PERSIST>, g, block, s, window, parent, n, pairs, k, vec, out, ovec, ds);
+    launch_windowed(k_query<E, MODE, PERSIST>, g, block, s, window, pdl != 0, parent, n, pairs, k, vec, out, ovec,
+                    ds, (int)(pdl == 2));
 }
 
 template <int MODE>
 static void query_inst(unsigned g, Launch cfg, cudaStream_t s, int* parent, int n,
                        const int* pairs, int64_t k, int vec, uint8_t* out, int ovec, DevState* ds) {
-#define CC_Q(E, P) query_one<E, MODE, P>(g, cfg.block, cfg.window, s, parent, n, pairs, k, vec, out, ovec, ds)
+#define CC_Q(E, P) query_one<E, MODE, P>(g, cfg.block, cfg.window, cfg.pdl, s, parent, n, pairs, k, vec, out, ovec, ds)
     const bool persist = cfg.query_variant == 1;
     switch (cfg.ept) {
         case 1: if (persist) CC_Q(1, true); else CC_Q(1, false); break;

@@ -36,6 +36,11 @@ OPTION_SETS = {
     "persistent_query_flat": {"query_variant": 1, "compress_every": 1, "block": 1024},
     "splitting_query": {"query_halving": 2, "compress_every": 0, "edges_per_thread": 4},
     "splitting_query_persistent": {"query_halving": 2, "compress_every": 0, "query_variant": 1},
+    "pdl_off": {"pdl": 0},
+    "pdl_early_persistent": {"pdl": 2, "update_variant": 2, "edges_per_thread": 4, "compress_every": 0,
+                             "query_halving": 1},
+    "pdl_early_query_persistent": {"pdl": 2, "query_variant": 1, "compress_every": 0, "l2_persist": 1},
+    "pdl_early_ept1": {"pdl": 2, "update_variant": 1, "edges_per_thread": 1, "compress_every": 2},
 }
 
 
