@@ -79,7 +79,13 @@ typedef enum {
     CC_OPT_PROFILE = 5,          /* 1: time every kernel with CUDA events on the handle's stream */
     CC_OPT_UPDATE_VARIANT = 6,   /* Bulk-Update kernel: 0 per-edge walks, 1 lockstep walks of all
                                     endpoints of a thread, 2 = 1 on a persistent grid that prefetches
-                                    the next edges (default 0) */
+                                    the next edges, 3 = 2 that also has the next chunk's first
+                                    parent reads in flight during this chunk's walks, 4 = two
+                                    kernels: a filter pass that reads every edge's first parents
+                                    and lists the edges whose parents differ (16 B each; the list,
+                                    room for the largest minibatch so far, is allocated on first
+                                    use and grown with one stream synchronisation), then a pass
+                                    that walks and hooks only the listed edges (default 0) */
     CC_OPT_L2_PERSIST = 7,       /* 1: ask L2 to keep the forest resident: the Bulk-Update and
                                     Bulk-Query kernels are launched with an access-policy window
                                     over the forest (a per-launch attribute; the stream is not
@@ -118,7 +124,9 @@ typedef enum {
                                     2 = as 1, but each thread's first pairs are read BEFORE that
                                     wait -- only for pair arrays that the kernel launched just
                                     before on the same stream does not write */
-    CC_OPT__COUNT = 18
+    CC_OPT_QUERY_PAIRS_PER_THREAD = 18, /* pairs per thread of the Bulk-Query kernel: 1, 2 or 4;
+                                    0 = as CC_OPT_EDGES_PER_THREAD (default) */
+    CC_OPT__COUNT = 19
 } cc_option;
 
 /* Kernel kinds reported by the launch counters and the profiler. */

@@ -51,7 +51,7 @@ struct DeviceScope {
 };
 
 const int64_t kDefaults[CC_OPT__COUNT] = {256, 2, 1, CC_COMPRESS_ALL, 0, 0, 0, 0,
-                                          512, 1, 65536, 1, 0, 0, 0, 0, 0, 1};
+                                          512, 1, 65536, 1, 0, 0, 0, 0, 0, 1, 0};
 
 }  // namespace
 
@@ -93,6 +93,12 @@ struct cc_ctx {
     unsigned* pcount = nullptr;   // device: [0] = |A''|, [1] = hooked flag
     int64_t last_nonloop = 0;
     int32_t last_rounds = 0;
+
+    // the two-pass Bulk-Update (update variant 4)
+    int4* live = nullptr;           // open edges of the current minibatch
+    int64_t live_cap = 0;           // in entries
+    unsigned* live_count = nullptr; // the two alternating list counters
+    uint64_t live_seq = 0;          // two-pass updates so far (selects the counter)
 
     // union by size (CC_OPT_LINK = 1)
     int* size = nullptr;                 // tree sizes, meaningful at roots
@@ -139,7 +145,8 @@ cc_status run(cc_ctx* c, int kind, const char* what, F&& launch) {
 cc::Launch cfg_of(const cc_ctx* c) {
     return cc::Launch{(int)c->opt[CC_OPT_BLOCK], (int)c->opt[CC_OPT_EDGES_PER_THREAD],
                       (int)c->opt[CC_OPT_UPDATE_VARIANT], (int)c->opt[CC_OPT_QUERY_VARIANT],
-                      c->window.num_bytes > 0 ? &c->window : nullptr, (int)c->opt[CC_OPT_PDL]};
+                      c->window.num_bytes > 0 ? &c->window : nullptr, (int)c->opt[CC_OPT_PDL],
+                      (int)c->opt[CC_OPT_QUERY_PAIRS_PER_THREAD]};
 }
 
 cc_status check_pairs(const int32_t* p, int64_t k, const char* name) {
@@ -169,6 +176,44 @@ cc_status do_compress(cc_ctx* c, int scope, const int32_t* edges, int64_t k) {
     return run(c, CC_K_COMPRESS_TOUCHED, "compress(touched)", [&] {
         return cc::launch_compress_touched(c->parent, (int)c->n, edges, k, c->ds, cfg_of(c), c->stream);
     });
+}
+
+// One Bulk-Update as a filter pass and a live-edge pass (update variant 4).
+// The list has room for k entries; growing it synchronises the stream once.
+cc_status split_update(cc_ctx* c, const int32_t* edges, int64_t k) {
+    cudaError_t e = cudaSuccess;
+    if (!c->live_count) {
+        e = cudaMalloc(&c->live_count, 2 * sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->live_count, 0, 2 * sizeof(unsigned), c->stream);
+        if (e != cudaSuccess) {
+            cudaFree(c->live_count);
+            c->live_count = nullptr;
+            cudaGetLastError();
+            return fail(CC_ERR_OOM, "update variant 4: list counters");
+        }
+    }
+    if (k > c->live_cap) {
+        int4* live = nullptr;
+        e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess) e = cudaMalloc(&live, sizeof(int4) * (size_t)k);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CC_ERR_OOM, "update variant 4: list of %lld edges", (long long)k);
+        }
+        cudaFree(c->live);
+        c->live = live;
+        c->live_cap = k;
+    }
+    const int sel = (int)(c->live_seq & 1u);
+    cc_status s = run(c, CC_K_UPDATE, "bulk_update (two passes)", [&] {
+        return cc::launch_update_split(c->parent, (int)c->n, edges, k, c->ds, cfg_of(c), c->live,
+                                       c->live_count, sel, c->stream);
+    });
+    if (s == CC_OK) {
+        c->live_seq++;
+        c->launches[CC_K_UPDATE]++;  // the second kernel
+    }
+    return s;
 }
 
 // Algorithm 2 as written, one Bulk-Update: relabel + filter, CC rounds, join.
@@ -362,6 +407,8 @@ cc_status cc_destroy(cc_ctx* c) {
         cudaFree(c->pcount);
         cudaFree(c->size);
         cudaFree(c->best);
+        cudaFree(c->live);
+        cudaFree(c->live_count);
         cc::bulk_find_free(c->bf);
         cudaFree(c->parent);
         cudaFree(c->ds);
@@ -425,6 +472,8 @@ cc_status cc_bulk_update(cc_ctx* c, const int32_t* edges, int64_t k) {
     c->fresh = false;
     if (c->opt[CC_OPT_UPDATE_SCHEDULE] == 1) {
         s = paper_update(c, edges, k);
+    } else if (c->opt[CC_OPT_UPDATE_VARIANT] == 4) {
+        s = split_update(c, edges, k);
     } else {
         s = run(c, CC_K_UPDATE, "bulk_update", [&] {
             return cc::launch_update(c->parent, (int)c->n, edges, k, c->ds, cfg_of(c), c->stream);
@@ -796,6 +845,9 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
         case CC_OPT_PDL:
             if (value < 0 || value > 2) return fail(CC_ERR_ARG, "pdl %lld: need 0, 1 or 2", (long long)value);
             break;
+        case CC_OPT_QUERY_PAIRS_PER_THREAD:
+            if (value != 0 && value != 1 && value != 2 && value != 4) return fail(CC_ERR_ARG, "query pairs per thread %lld: need 0, 1, 2 or 4", (long long)value);
+            break;
         case CC_OPT_PROFILE:
             if (value != 0 && value != 1) return fail(CC_ERR_ARG, "option %d takes 0 or 1", option);
             break;
@@ -837,7 +889,7 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
             if (value != 0 && value != 1) return fail(CC_ERR_ARG, "update schedule %lld: need 0 or 1", (long long)value);
             break;
         case CC_OPT_UPDATE_VARIANT:
-            if (value < 0 || value > 2) return fail(CC_ERR_ARG, "update variant %lld: need 0, 1 or 2", (long long)value);
+            if (value < 0 || value > 4) return fail(CC_ERR_ARG, "update variant %lld: need 0..4", (long long)value);
             break;
         case CC_OPT_L2_PERSIST: {
             if (value != 0 && value != 1) return fail(CC_ERR_ARG, "option %d takes 0 or 1", option);

@@ -28,10 +28,13 @@ struct DevState {
 struct Launch {
     int block;        // threads per block, multiple of 32
     int ept;          // edges (pairs) per thread: 1, 2 or 4
-    int variant = 0;  // update kernel: 0 per-edge walks, 1 lockstep walks, 2 persistent + prefetch
+    int variant = 0;  // update kernel: 0 per-edge walks, 1 lockstep walks, 2 persistent + prefetch,
+                      // 3 persistent + two-stage prefetch (edges two chunks ahead, parents one),
+                      // 4 filter pass + live-edge pass (launch_update_split)
     int query_variant = 0;  // query kernel: 0 one chunk per thread, 1 persistent + prefetch
     const cudaAccessPolicyWindow* window = nullptr;  // L2 window over the forest, or none
     int pdl = 0;  // programmatic dependent launch: 0 off, 1 wait first, 2 first pairs before the wait
+    int qept = 0; // pairs per thread of the query kernel (0 = ept)
 };
 
 // Alignment class of a pair array: 2 = 16-byte, 1 = 8-byte, 0 = 4-byte.
@@ -49,6 +52,14 @@ cudaError_t launch_reset(int* parent, int64_t n, int block, cudaStream_t s);
 
 cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevState* ds,
                           Launch cfg, cudaStream_t s);
+
+// Bulk-Update as two kernels (update variant 4): a filter pass that reads the
+// first parents of every edge and lists the edges whose parents differ as
+// (u, v, parent[u], parent[v]) in live[] (room for k entries), then a pass
+// that walks and hooks the listed edges. count[2]: list counters, both zero
+// initially; sel alternates 0, 1, 0, ... between consecutive calls.
+cudaError_t launch_update_split(int* parent, int n, const int* edges, int64_t k, DevState* ds, Launch cfg,
+                                int4* live, unsigned* count, int sel, cudaStream_t s);
 
 // mode: 0 read-only finds, 1 finds with path halving, 2 flat forest (parent
 // equality decides), 3 lockstep finds with path splitting.

@@ -183,6 +183,239 @@ k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t
     if ((threadIdx.x & 31) == 0 && made) atomicAdd(&ds->unions, (unsigned long long)made);
 }
 
+// --- VARIANT 3: the persistent grid with a two-stage prefetch -------------
+
+// Bit i set when this thread's edge i at e0 exists and has both endpoints in
+// range; range errors are flagged here, once per chunk.
+template <int E>
+__device__ __forceinline__ unsigned edge_mask(int n, const int (&u)[E], const int (&v)[E], int64_t e0,
+                                              int64_t k, DevState* __restrict__ ds) {
+    unsigned m = 0;
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        if (e0 + i >= k) continue;
+        if (in_range(u[i], n) && in_range(v[i], n)) m |= 1u << i;
+        else bad = true;
+    }
+    if (bad) flag(ds, ST_RANGE);
+    return m;
+}
+
+// The first parent reads of the edges in m, all issued together (an edge not
+// in m reads nothing and keeps its endpoints as their own parents).
+template <int E>
+__device__ __forceinline__ void gather_parents(const int* parent, unsigned m, const int (&u)[E],
+                                               const int (&v)[E], int (&pu)[E], int (&pv)[E]) {
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        const bool on = (m >> i) & 1u;
+        pu[i] = on ? parent[u[i]] : u[i];
+        pv[i] = on ? parent[v[i]] : v[i];
+    }
+}
+
+// The rest of the fused pass for edges whose first parents pu, pv were read
+// earlier, possibly before other links of this minibatch: a parent read then
+// is still an ancestor now (links only put roots under roots, and splitting
+// only repoints a node at an ancestor), so walking on from it reaches the
+// current root, and equal values still prove the endpoints joined.
+template <int E>
+__device__ __forceinline__ int walk_and_hook(int* parent, unsigned m, const int (&u)[E], const int (&v)[E],
+                                             const int (&pu)[E], const int (&pv)[E], DevState* ds) {
+    int x[2 * E], p[2 * E];
+    bool live[E];
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        live[i] = ((m >> i) & 1u) && pu[i] != pv[i];
+        x[2 * i] = u[i];
+        x[2 * i + 1] = v[i];
+        p[2 * i] = live[i] ? pu[i] : u[i];
+        p[2 * i + 1] = live[i] ? pv[i] : v[i];
+    }
+    walk_split<2 * E>(parent, x, p, ds);
+    int made = 0;
+#pragma unroll
+    for (int i = 0; i < E; i++)
+        if (live[i]) made += hook(parent, x[2 * i], x[2 * i + 1], ds);
+    return made;
+}
+
+// Persistent grid over chunks of E edges per thread. While the walks and
+// hooks of chunk c run, the first parent reads of chunk c+1 and the edge
+// loads of chunk c+2 are already in flight, so a warp waiting on its deepest
+// walk still has the next chunk's gathers outstanding. early: as for k_update.
+template <int E>
+__global__ void __launch_bounds__(1024)
+k_update_deep(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
+              DevState* __restrict__ ds, int early) {
+    pdl_trigger();
+    if (!early) pdl_wait();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * E;
+    int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
+    int made = 0;
+    int u0[E] = {}, v0[E] = {}, u1[E] = {}, v1[E] = {};
+    if (e0 < k) load_pairs<E>(edges, e0, k, vec, u0, v0);
+    if (e0 + stride < k) load_pairs<E>(edges, e0 + stride, k, vec, u1, v1);
+    if (early) pdl_wait();
+    unsigned m0 = e0 < k ? edge_mask<E>(n, u0, v0, e0, k, ds) : 0u;
+    int pu0[E], pv0[E];
+    gather_parents<E>(parent, m0, u0, v0, pu0, pv0);
+    while (e0 < k) {
+        const int64_t e1 = e0 + stride, e2 = e1 + stride;
+        const unsigned m1 = e1 < k ? edge_mask<E>(n, u1, v1, e1, k, ds) : 0u;
+        int pu1[E], pv1[E];
+        gather_parents<E>(parent, m1, u1, v1, pu1, pv1);
+        int u2[E] = {}, v2[E] = {};
+        if (e2 < k) load_pairs<E>(edges, e2, k, vec, u2, v2);
+        made += walk_and_hook<E>(parent, m0, u0, v0, pu0, pv0, ds);
+#pragma unroll
+        for (int i = 0; i < E; i++) {
+            u0[i] = u1[i]; v0[i] = v1[i]; pu0[i] = pu1[i]; pv0[i] = pv1[i];
+            u1[i] = u2[i]; v1[i] = v2[i];
+        }
+        m0 = m1;
+        e0 = e1;
+    }
+    made = __reduce_add_sync(0xffffffffu, made);
+    if ((threadIdx.x & 31) == 0 && made) atomicAdd(&ds->unions, (unsigned long long)made);
+}
+
+template <int E>
+static int resident_blocks_deep(int block) {
+    static int cached[33] = {};
+    int& c = cached[block / 32];
+    if (!c) {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_deep<E>, block, 0);
+        c = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    }
+    return c;
+}
+
+template <int E>
+static void update_deep_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
+                             int block, const cudaAccessPolicyWindow* window, int pdl, cudaStream_t s) {
+    int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
+    const int64_t cap = resident_blocks_deep<E>(block);
+    if (g > cap) g = cap;
+    launch_windowed(k_update_deep<E>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k, vec, ds,
+                    (int)(pdl == 2));
+}
+
+// --- VARIANT 4: filter pass + live-edge pass ------------------------------
+//
+// Once the forest is shallow, almost every edge of a minibatch already has
+// parent[u] == parent[v] (its endpoints were joined before), and only a few
+// percent need walks and a hook. Pass 1 streams all edges and does only those
+// first parent reads -- every warp's loads are independent, so the pass runs
+// at the rate of the gathers -- and appends each edge that is still open as
+// (u, v, parent[u], parent[v]) to a compact list. Pass 2 walks and hooks only
+// the listed edges, from the parents pass 1 read (still ancestors; see
+// walk_and_hook). The two list counters alternate between minibatches: pass 1
+// of minibatch i appends through count[sel] and zeroes count[sel ^ 1] for
+// minibatch i + 1, after the wait that orders it behind everything before it.
+
+template <int E>
+__global__ void __launch_bounds__(1024)
+k_update_filter(const int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
+                int4* __restrict__ live, unsigned* __restrict__ count, int sel, DevState* __restrict__ ds,
+                int early) {
+    pdl_trigger();
+    if (!early) pdl_wait();
+    const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
+    int u[E] = {}, v[E] = {};
+    if (e0 < k) load_pairs<E>(edges, e0, k, vec, u, v);
+    if (early) pdl_wait();
+    if (blockIdx.x == 0 && threadIdx.x == 0) count[sel ^ 1] = 0u;
+    const unsigned m = e0 < k ? edge_mask<E>(n, u, v, e0, k, ds) : 0u;
+    int pu[E], pv[E];
+    gather_parents<E>(parent, m, u, v, pu, pv);
+    unsigned open = 0;
+#pragma unroll
+    for (int i = 0; i < E; i++)
+        if (((m >> i) & 1u) && pu[i] != pv[i]) open |= 1u << i;
+    // one atomic per warp: an exclusive scan of the lanes' open counts
+    const unsigned lane = threadIdx.x & 31u;
+    const int mine = __popc(open);
+    int incl = mine;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= (unsigned)d) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    unsigned base = 0;
+    if (lane == 31) base = atomicAdd(count + sel, (unsigned)total);
+    base = __shfl_sync(0xffffffffu, base, 31) + (unsigned)(incl - mine);
+#pragma unroll
+    for (int i = 0; i < E; i++)
+        if ((open >> i) & 1u) live[base++] = make_int4(u[i], v[i], pu[i], pv[i]);
+}
+
+// Pass 2: two listed edges per thread per step, their four walks in lockstep.
+__global__ void __launch_bounds__(1024)
+k_update_live(int* __restrict__ parent, const int4* __restrict__ live, const unsigned* __restrict__ count,
+              int sel, DevState* __restrict__ ds) {
+    pdl_trigger();
+    pdl_wait();
+    const int64_t m = count[sel];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 2;
+    int made = 0;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2; i < m; i += stride) {
+        const int4 a = live[i];
+        const int4 b = i + 1 < m ? live[i + 1] : a;
+        const unsigned on = i + 1 < m ? 3u : 1u;
+        const int u[2] = {a.x, b.x}, v[2] = {a.y, b.y}, pu[2] = {a.z, b.z}, pv[2] = {a.w, b.w};
+        made += walk_and_hook<2>(parent, on, u, v, pu, pv, ds);
+    }
+    made = __reduce_add_sync(0xffffffffu, made);
+    if ((threadIdx.x & 31) == 0 && made) atomicAdd(&ds->unions, (unsigned long long)made);
+}
+
+template <int E>
+static void update_filter_inst(const int* edges, int64_t k, int vec, const int* parent, int n, int4* live,
+                               unsigned* count, int sel, DevState* ds, int block,
+                               const cudaAccessPolicyWindow* window, int pdl, cudaStream_t s) {
+    const int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
+    launch_windowed(k_update_filter<E>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k, vec,
+                    live, count, sel, ds, (int)(pdl == 2));
+}
+
+cudaError_t launch_update_split(int* parent, int n, const int* edges, int64_t k, DevState* ds, Launch cfg,
+                                int4* live, unsigned* count, int sel, cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    const int vec = pair_vec(edges);
+    switch (cfg.ept) {
+        case 1: update_filter_inst<1>(edges, k, vec, parent, n, live, count, sel, ds, cfg.block, cfg.window, cfg.pdl, s); break;
+        case 2: update_filter_inst<2>(edges, k, vec, parent, n, live, count, sel, ds, cfg.block, cfg.window, cfg.pdl, s); break;
+        case 4: update_filter_inst<4>(edges, k, vec, parent, n, live, count, sel, ds, cfg.block, cfg.window, cfg.pdl, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // pass 2 on a grid of resident CTAs, capped by the most it could have to do
+    static int per_sm[33] = {};
+    static int sms = 0;
+    int& ps = per_sm[cfg.block / 32];
+    if (!ps) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_update_live, cfg.block, 0);
+        if (ps < 1) ps = 1;
+        if (sms < 1) sms = 1;
+    }
+    int64_t g = (k + 2LL * cfg.block - 1) / (2LL * cfg.block);
+    if (g > (int64_t)ps * sms) g = (int64_t)ps * sms;
+    launch_windowed(k_update_live, (unsigned)g, cfg.block, s, cfg.window, cfg.pdl != 0, parent,
+                    (const int4*)live, (const unsigned*)count, sel, ds);
+    return cudaGetLastError();
+}
+
 template <int E, int VARIANT>
 static int resident_blocks(int block) {
     static int cached[33] = {};
@@ -224,6 +457,9 @@ cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevSt
         case 17: CC_UPD(1, 2); break;
         case 18: CC_UPD(2, 2); break;
         case 20: CC_UPD(4, 2); break;
+        case 25: update_deep_inst<1>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, s); break;
+        case 26: update_deep_inst<2>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, s); break;
+        case 28: update_deep_inst<4>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, s); break;
         default: return cudaErrorInvalidValue;
     }
 #undef CC_UPD
@@ -418,6 +654,7 @@ static void query_inst(unsigned g, Launch cfg, cudaStream_t s, int* parent, int 
 cudaError_t launch_query(int* parent, int n, const int* pairs, int64_t k, uint8_t* out,
                          DevState* ds, int mode, Launch cfg, cudaStream_t s) {
     if (k <= 0) return cudaSuccess;
+    if (cfg.qept) cfg.ept = cfg.qept;
     const int vec = pair_vec(pairs);
     const int ovec = (reinterpret_cast<uintptr_t>(out) % cfg.ept) == 0;
     const unsigned g = blocks_for(k, (int64_t)cfg.ept * cfg.block);

@@ -35,7 +35,7 @@ from . import inputs as I
 CACHE = Path(__file__).resolve().parent / "tuned.json"
 
 PLAIN_SPACE = {
-    "update_variant": [0, 1, 2],
+    "update_variant": [0, 1, 2, 3, 4],
     "edges_per_thread": [1, 2, 4],
     "block": [128, 256, 512, 1024],
     "compress_every": [0, 1, 2, 4, 8, 16],
@@ -44,10 +44,11 @@ PLAIN_SPACE = {
     "l2_persist": [0, 1],
     "query_variant": [0, 1],
     "pdl": [0, 1, 2],
+    "query_pairs_per_thread": [0, 1, 2, 4],
 }
 PLAIN_START = {"update_variant": 0, "edges_per_thread": 2, "block": 256, "compress_every": 1,
                "compress_scope": 0, "query_halving": 0, "l2_persist": 0, "query_variant": 0,
-               "pdl": 1}
+               "pdl": 1, "query_pairs_per_thread": 0}
 
 SEG_SPACE = {
     "seg_block": [128, 256, 512, 1024],

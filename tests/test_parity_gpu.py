@@ -37,6 +37,16 @@ OPTION_SETS = {
     "splitting_query": {"query_halving": 2, "compress_every": 0, "edges_per_thread": 4},
     "splitting_query_persistent": {"query_halving": 2, "compress_every": 0, "query_variant": 1},
     "pdl_off": {"pdl": 0},
+    "two_pass_ept4": {"update_variant": 4, "edges_per_thread": 4, "compress_every": 0},
+    "two_pass_ept1_pdl0": {"update_variant": 4, "edges_per_thread": 1, "pdl": 0, "compress_every": 2},
+    "two_pass_ept2_pdl2_b1024": {"update_variant": 4, "edges_per_thread": 2, "pdl": 2, "block": 1024,
+                                 "compress_every": 0, "query_pairs_per_thread": 4},
+    "query_ept2_update_ept4": {"edges_per_thread": 4, "query_pairs_per_thread": 2, "compress_every": 0,
+                               "update_variant": 2, "pdl": 2},
+    "query_ept1_halving": {"query_pairs_per_thread": 1, "query_halving": 1, "compress_every": 0},
+    "deep_prefetch_ept4": {"update_variant": 3, "edges_per_thread": 4, "compress_every": 0},
+    "deep_prefetch_ept2_pdl2": {"update_variant": 3, "edges_per_thread": 2, "compress_every": 0, "pdl": 2},
+    "deep_prefetch_ept1_b1024": {"update_variant": 3, "edges_per_thread": 1, "block": 1024, "compress_every": 3},
     "pdl_early_persistent": {"pdl": 2, "update_variant": 2, "edges_per_thread": 4, "compress_every": 0,
                              "query_halving": 1},
     "pdl_early_query_persistent": {"pdl": 2, "query_variant": 1, "compress_every": 0, "l2_persist": 1},
