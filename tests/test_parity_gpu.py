@@ -107,14 +107,16 @@ def test_uniform_small_every_batch(cc, opts):
 
 @pytest.mark.parametrize("opts", ["default", "ept1_b64", "no_compress", "touched_compress",
                                   "lockstep_ept4_nocompress", "persistent_ept4",
-                                  "persistent_query_halving", "splitting_query"])
+                                  "persistent_query_halving", "splitting_query", "deep_prefetch_ept2_pdl2",
+                                  "two_pass_ept4", "query_ept2_update_ept4"])
 def test_rmat_small(cc, opts):
     s = I.rmat_stream(scale=16, m=1 << 20, batch=(1 << 16) + 3, q=(1 << 16) - 5, seed=1)
     run_stream(cc, s, OPTION_SETS[opts], label_every=4, check_invariants=True)
 
 
 @pytest.mark.parametrize("opts", ["default", "no_compress", "ept4_b1024", "compress_every3",
-                                  "lockstep", "persistent_ept1_b1024", "splitting_query"])
+                                  "lockstep", "persistent_ept1_b1024", "splitting_query",
+                                  "deep_prefetch_ept1_b1024", "two_pass_ept1_pdl0"])
 def test_grid_small(cc, opts):
     s = I.grid_stream(512, 512, batch=(1 << 14) + 1, q=1 << 14, seed=2)
     ref = run_stream(cc, s, OPTION_SETS[opts], label_every=8, check_invariants=True)
