@@ -20,6 +20,7 @@ compression) on a bounded sample of each step's minibatch.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -371,6 +372,7 @@ def run_serving(args, rank: int, world: int, local_rank: int, dist) -> dict:
     def serve(rate: float | None):
         f = cc.Forest(s.n, **opts)
         with cc.Server(f) as srv:
+            gc.disable()                         # no collector pause inside the enqueue loop
             t0 = time.perf_counter()
             for r, (kind, d, o) in zip(reqs, views):
                 if rate is not None:
@@ -380,6 +382,7 @@ def run_serving(args, rank: int, world: int, local_rank: int, dist) -> dict:
                 srv.enqueue(kind, d, o)
             srv.drain()
             dt = time.perf_counter() - t0
+            gc.enable()
             lat = srv.latencies()
             st = srv.stats()
         labels = f.labels()

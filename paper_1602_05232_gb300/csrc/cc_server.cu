@@ -72,7 +72,11 @@ struct cc_server {
     bool merge = true;
 
     std::mutex mu;
-    std::condition_variable cv;
+    // one condition per kind of waiter, so that a notification wakes only
+    // the thread that can act on it
+    std::condition_variable cv_work;  // worker: new requests, ring space, stop
+    std::condition_variable cv_reap;  // completion thread: launched groups, stop
+    std::condition_variable cv_done;  // cc_server_wait / drain / destroy: completions
     std::deque<Req> reqs;
     int64_t next_launch = 0, completed = 0, groups = 0;
     int64_t n_upd = 0, n_qry = 0, edges = 0, pairs = 0;
@@ -94,7 +98,9 @@ void fail_worker(cc_server* s, cudaError_t e, const char* what) {
         s->err = CC_ERR_CUDA;
         s->errmsg = std::string(what) + ": " + cudaGetErrorString(e);
     }
-    s->cv.notify_all();
+    s->cv_work.notify_all();
+    s->cv_reap.notify_all();
+    s->cv_done.notify_all();
 }
 
 // A group's work is complete: stamp its requests, free ring ranges in order.
@@ -112,43 +118,51 @@ void mark_done(cc_server* s, Group* g, double t) {
         delete f;
         s->inflight.pop_front();
     }
-    s->cv.notify_all();
+    s->cv_done.notify_all();
+    s->cv_work.notify_one();  // ring space for a group that did not fit
 }
 
-// Completion thread: polls the events of the groups in flight (a dedicated
-// thread keeps the time from completion to notice to a few microseconds).
+// Completion thread: takes the oldest launched group that is not done under
+// the lock, then polls its event with the lock released (the worker and the
+// enqueuing threads never wait behind the poll), so the time from completion
+// to notice stays at a few microseconds. Groups complete in launch order
+// except that an update group may finish while an earlier query group's
+// answers are still being copied out; such a group is noticed right after
+// that copy. Only this thread marks groups done, and a group is freed only
+// once done, so the pointer stays valid while it is polled.
 void reaper_loop(cc_server* s) {
     cudaSetDevice(s->device);
-    std::vector<Group*> watch;
     for (;;) {
+        Group* g = nullptr;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv.wait(lk, [&] {
-                if (s->err != CC_OK) return true;
-                for (Group* g : s->inflight)
-                    if (g->launched && !g->done) return true;
+            auto oldest = [&]() -> Group* {
+                for (Group* x : s->inflight)
+                    if (!x->done) return x->launched ? x : nullptr;
+                return nullptr;
+            };
+            s->cv_reap.wait(lk, [&] {
+                if (s->err != CC_OK || oldest()) return true;
                 return s->stop && s->next_launch >= (int64_t)s->reqs.size() && s->inflight.empty();
             });
             if (s->err != CC_OK) return;
-            watch.clear();
-            for (Group* g : s->inflight)
-                if (g->launched && !g->done) watch.push_back(g);
-            if (watch.empty()) return;  // stopping, nothing left
+            g = oldest();
+            if (!g) return;  // stopping, nothing left
         }
-        bool any = false;
-        for (Group* g : watch) {
-            const cudaError_t q = cudaEventQuery(g->ev);  // no lock held
-            if (q == cudaSuccess) {
-                const double t = now_s();
-                std::lock_guard<std::mutex> lk(s->mu);
-                mark_done(s, g, t);
-                any = true;
-            } else if (q != cudaErrorNotReady) {
-                fail_worker(s, q, "serve: completion");
-                return;
-            }
+        // poll every ~2 us: often enough for latency, rarely enough that the
+        // driver calls of the worker thread do not queue behind the queries
+        cudaError_t q;
+        while ((q = cudaEventQuery(g->ev)) == cudaErrorNotReady) {
+            const double t_next = now_s() + 2e-6;
+            while (now_s() < t_next) std::this_thread::yield();
         }
-        if (!any) std::this_thread::yield();
+        if (q != cudaSuccess) {
+            fail_worker(s, q, "serve: completion");
+            return;
+        }
+        const double t = now_s();
+        std::lock_guard<std::mutex> lk(s->mu);
+        mark_done(s, g, t);
     }
 }
 
@@ -185,7 +199,7 @@ void worker_loop(cc_server* s) {
         Group* g = nullptr;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv.wait(lk, [&] { return s->stop || s->err != CC_OK || s->next_launch < (int64_t)s->reqs.size(); });
+            s->cv_work.wait(lk, [&] { return s->stop || s->err != CC_OK || s->next_launch < (int64_t)s->reqs.size(); });
             if (s->err != CC_OK) return;
             if (s->next_launch >= (int64_t)s->reqs.size()) return;  // stop, nothing left
             for (;;) {
@@ -202,7 +216,7 @@ void worker_loop(cc_server* s) {
                 // shrink it until its staging range fits; else wait for room
                 while (!ring_alloc(s, total, &b) && last - first > 1) total -= s->reqs[--last].k;
                 if (ring_alloc(s, total, &b)) break;
-                s->cv.wait(lk);
+                s->cv_work.wait(lk);
                 if (s->err != CC_OK) return;
             }
             g = new Group{s, first, last, b, b + total};
@@ -282,7 +296,7 @@ void worker_loop(cc_server* s) {
         {
             std::lock_guard<std::mutex> lk(s->mu);
             g->launched = true;
-            s->cv.notify_all();
+            s->cv_reap.notify_one();
         }
     }
 }
@@ -355,7 +369,7 @@ cc_status cc_server_enqueue(cc_server* s, int32_t kind, const int32_t* data, int
     s->reqs.push_back(r);
     if (kind == CC_OP_UPDATE) { s->n_upd++; s->edges += k; } else { s->n_qry++; s->pairs += k; }
     if (ticket) *ticket = (uint64_t)(s->reqs.size() - 1);
-    s->cv.notify_all();
+    s->cv_work.notify_one();
     return CC_OK;
 }
 
@@ -363,7 +377,7 @@ cc_status cc_server_wait(cc_server* s, uint64_t ticket, double* latency_s) {
     if (!s) return server_fail(CC_ERR_ARG, "cc_server_wait: null server");
     std::unique_lock<std::mutex> lk(s->mu);
     if (ticket >= s->reqs.size()) return server_fail(CC_ERR_ARG, "cc_server_wait: unknown ticket");
-    s->cv.wait(lk, [&] { return s->reqs[ticket].done || s->err != CC_OK; });
+    s->cv_done.wait(lk, [&] { return s->reqs[ticket].done || s->err != CC_OK; });
     if (s->err != CC_OK) return server_fail(s->err, s->errmsg.c_str());
     if (latency_s) *latency_s = s->reqs[ticket].t_done - s->reqs[ticket].t_arrive;
     return CC_OK;
@@ -372,7 +386,7 @@ cc_status cc_server_wait(cc_server* s, uint64_t ticket, double* latency_s) {
 cc_status cc_server_drain(cc_server* s) {
     if (!s) return server_fail(CC_ERR_ARG, "cc_server_drain: null server");
     std::unique_lock<std::mutex> lk(s->mu);
-    s->cv.wait(lk, [&] { return s->completed == (int64_t)s->reqs.size() || s->err != CC_OK; });
+    s->cv_done.wait(lk, [&] { return s->completed == (int64_t)s->reqs.size() || s->err != CC_OK; });
     if (s->err != CC_OK) return server_fail(s->err, s->errmsg.c_str());
     return CC_OK;
 }
@@ -405,14 +419,15 @@ cc_status cc_server_destroy(cc_server* s) {
     cc_status st = CC_OK;
     {
         std::unique_lock<std::mutex> lk(s->mu);
-        s->cv.wait(lk, [&] { return s->completed == (int64_t)s->reqs.size() || s->err != CC_OK; });
+        s->cv_done.wait(lk, [&] { return s->completed == (int64_t)s->reqs.size() || s->err != CC_OK; });
         s->stop = true;
-        s->cv.notify_all();
+        s->cv_work.notify_all();
+        s->cv_reap.notify_all();
     }
     if (s->worker.joinable()) s->worker.join();
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        s->cv.notify_all();
+        s->cv_reap.notify_all();
     }
     if (s->reaper.joinable()) s->reaper.join();
     int prev = 0;
