@@ -818,10 +818,34 @@ def cpu_baseline(s, edges: np.ndarray, pairs: np.ndarray, eoff, qoff, seconds: f
         e_done += len(e)
         q_done += len(q)
         b += 1
+    ncpu = os.cpu_count()
     return {"value": round(e_done / t_total, 1), "unit": "edges/s", "cores": 1, "kind": "oracle",
             "sample": f"first {b} of {s.batches} minibatches ({e_done} edges + {q_done} query "
                       f"pairs) from the empty graph, {t_total:.1f} s on one host core",
-            "host_cores_available": os.cpu_count()}
+            "host_cores_available": ncpu, "host": host_info(),
+            "note": f"the oracle (a sequential union-find) uses 1 of {ncpu} host cores"}
+
+
+def host_info() -> dict:
+    """CPU model (from /proc/cpuinfo) and the process's CPU affinity."""
+    model = None
+    try:
+        keys = {}
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            k, v = k.strip(), v.strip()
+            if k in ("model name", "CPU implementer", "CPU part") and k not in keys:
+                keys[k] = v
+        model = keys.get("model name") or (
+            f"implementer {keys.get('CPU implementer')} part {keys.get('CPU part')}" if keys else None)
+    except OSError:
+        pass
+    try:
+        aff = sorted(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        aff = []
+    return {"cpu_model": model, "affinity_cpus": len(aff),
+            "affinity": f"{aff[0]}-{aff[-1]}" if aff and aff == list(range(aff[0], aff[-1] + 1)) else aff}
 
 
 def run_reference(args, rank: int, world: int) -> dict | None:
@@ -874,7 +898,8 @@ def run_reference(args, rank: int, world: int) -> dict | None:
                        "sample": f"each step applies the first 1/{frac} of its minibatch's edges "
                                  f"and queries the first 1/{frac} of its pairs"},
             "cpu_baseline": {"value": round(v, 1), "unit": "edges/s", "cores": 1, "kind": "oracle",
-                             "sample": f"1/{frac} of every minibatch, {args.steps} steps"},
+                             "sample": f"1/{frac} of every minibatch, {args.steps} steps",
+                             "host_cores_available": os.cpu_count(), "host": host_info()},
             "e2e": {"value": round(v, 1), "unit": "edges/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
