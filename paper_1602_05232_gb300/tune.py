@@ -83,10 +83,12 @@ def _store(workload: str, best: dict, ms: float, table: list) -> None:
     CACHE.write_text(json.dumps(d, indent=1, sort_keys=True) + "\n")
 
 
-def coordinate_descent(space: dict, start: dict, evaluate, rounds: int = 2, finalists: int = 3,
+def coordinate_descent(space: dict, start, evaluate, rounds: int = 2, finalists: int = 3,
                        log=None) -> tuple[dict, float, list]:
     """Minimise evaluate(options) over the product space by sweeping one
-    parameter at a time. Returns (best options, time, [(options, time)])."""
+    parameter at a time, from one start point or from each of a list of them
+    (sharing the measurements); the best few points seen are timed again and
+    the fastest wins. Returns (best options, time, [(options, time)])."""
     seen: dict[str, float] = {}
 
     def ev(o):
@@ -97,23 +99,39 @@ def coordinate_descent(space: dict, start: dict, evaluate, rounds: int = 2, fina
                 log(o, seen[key])
         return seen[key]
 
-    best = dict(start)
-    best_t = ev(best)
-    for _ in range(rounds):
-        improved = False
-        for name, values in space.items():
-            for v in values:
-                cand = dict(best, **{name: v})
-                t = ev(cand)
-                if t < best_t:
-                    best, best_t, improved = cand, t, True
-        if not improved:
-            break
+    for s0 in ([start] if isinstance(start, dict) else list(start)):
+        best = dict(s0)
+        best_t = ev(best)
+        for _ in range(rounds):
+            improved = False
+            for name, values in space.items():
+                for v in values:
+                    cand = dict(best, **{name: v})
+                    t = ev(cand)
+                    if t < best_t:
+                        best, best_t, improved = cand, t, True
+            if not improved:
+                break
     table = [(json.loads(k), t) for k, t in seen.items()]
     top = sorted(table, key=lambda x: x[1])[:finalists]
     retimed = [(o, min(t, evaluate(o))) for o, t in top]
     best, best_t = min(retimed, key=lambda x: x[1])
     return best, best_t, table
+
+
+def starts_for(workload: str, space: dict, default: dict) -> list[dict]:
+    """The default start point and, when this device has a stored result for
+    the workload, that result too (completed with the defaults for options it
+    predates, and only if every value is still in the space): descent from a
+    single point can settle in a worse local optimum, and a retune should not
+    end up slower than what is stored."""
+    starts = [dict(default)]
+    cached = tuned_options(workload)
+    if cached:
+        cand = {k: cached.get(k, default[k]) for k in default}
+        if all(cand[k] in space[k] for k in space if k in cand) and cand != starts[0]:
+            starts.append(cand)
+    return starts
 
 
 # ------------------------------------------------------------ plain form
@@ -153,6 +171,7 @@ class PlainBench:
 
 
 def tune_plain(stream_obj, space=PLAIN_SPACE, start=PLAIN_START, repeats: int = 3, log=None):
+    """start: one option dict or a list of them (see coordinate_descent)."""
     bench = PlainBench(stream_obj)
     return coordinate_descent(space, start, lambda o: bench.time(o, repeats), log=log)
 
@@ -222,9 +241,9 @@ def main(argv=None) -> int:
         form, obj = WORKLOADS[wl]()
         log = lambda o, t: print(f"  {wl}: {t:9.3f} ms  {o}", flush=True)
         if form == "plain":
-            best, t, table = tune_plain(obj, log=log)
+            best, t, table = tune_plain(obj, start=starts_for(wl, PLAIN_SPACE, PLAIN_START), log=log)
         else:
-            best, t, table = tune_segmented(obj, log=log)
+            best, t, table = tune_segmented(obj, start=starts_for(wl, SEG_SPACE, SEG_START), log=log)
         print(json.dumps({"workload": wl, "device": device_name(), "best": best,
                           "ms_per_pass": round(t, 4), "evaluated": len(table)}), flush=True)
         if args.write:

@@ -34,3 +34,30 @@ def test_coordinate_descent_retimes_finalists():
 
 def test_tuned_options_missing_device_is_none():
     assert tune.tuned_options("rmat", device="no such device") is None
+
+
+def test_coordinate_descent_from_several_starts_escapes_a_local_optimum():
+    # two basins: from the default start, one-coordinate moves stop at
+    # (a=1, b=1) with cost 2; the global minimum (a=4, b=4) needs a second start
+    space = {"a": [1, 2, 3, 4], "b": [1, 2, 3, 4]}
+    cost_table = {(1, 1): 2.0, (4, 4): 1.0}
+
+    def cost(o):
+        return cost_table.get((o["a"], o["b"]), 10.0)
+
+    best, t, _ = tune.coordinate_descent(space, {"a": 1, "b": 1}, cost)
+    assert best == {"a": 1, "b": 1}
+    best, t, _ = tune.coordinate_descent(space, [{"a": 1, "b": 1}, {"a": 4, "b": 3}], cost)
+    assert best == {"a": 4, "b": 4} and t == 1.0
+
+
+def test_starts_include_the_stored_result(monkeypatch):
+    space = {"x": [1, 2, 3], "y": [0, 1]}
+    default = {"x": 1, "y": 0, "fixed": 7}
+    monkeypatch.setattr(tune, "tuned_options", lambda wl, device=None: {"x": 3})
+    starts = tune.starts_for("w", space, default)
+    assert starts == [default, {"x": 3, "y": 0, "fixed": 7}]   # completed with the defaults
+    monkeypatch.setattr(tune, "tuned_options", lambda wl, device=None: {"x": 9})
+    assert tune.starts_for("w", space, default) == [default]     # value no longer in the space
+    monkeypatch.setattr(tune, "tuned_options", lambda wl, device=None: None)
+    assert tune.starts_for("w", space, default) == [default]
