@@ -57,6 +57,24 @@ static void launch_windowed(void (*kernel)(Params...), unsigned grid, int block,
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 
+// A persistent grid for KERNEL at `block` threads (no dynamic shared memory):
+// resident CTAs per SM x SMs of the current device. Cached per host thread,
+// device and block size, so neither threads nor different GPUs share an entry.
+template <auto KERNEL>
+static int resident_grid(int block) {
+    thread_local int cache[16][33] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int* slot = (dev >= 0 && dev < 16 && block > 0 && block <= 1024) ? &cache[dev][block / 32] : nullptr;
+    if (slot && *slot) return *slot;
+    int per_sm = 0, sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, KERNEL, block, 0);
+    const int c = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    if (slot) *slot = c;
+    return c;
+}
+
 // ------------------------------------------------------------------ reset
 
 // parent[v] = v: n singletons, the empty graph G_0.
@@ -101,7 +119,7 @@ __device__ __forceinline__ int update_edges(int* __restrict__ parent, int n,
         }
     }
     if (bad) flag(ds, ST_RANGE);
-    if (VARIANT == 0) {
+    if constexpr (VARIANT == 0) {
         int pu[E], pv[E];
 #pragma unroll
         for (int i = 0; i < E; i++) {
@@ -116,30 +134,31 @@ __device__ __forceinline__ int update_edges(int* __restrict__ parent, int n,
             made += hook(parent, ru, rv, ds);
         }
         return made;
-    }
-    // lockstep: chain c = 2i (u side) and 2i+1 (v side); finished when p >= x
-    int x[2 * E], p[2 * E];
+    } else {
+        // lockstep: chain c = 2i (u side) and 2i+1 (v side); finished when p >= x
+        int x[2 * E], p[2 * E];
 #pragma unroll
-    for (int i = 0; i < E; i++) {
-        x[2 * i] = ok[i] ? u[i] : 0;
-        x[2 * i + 1] = ok[i] ? v[i] : 0;
-    }
-#pragma unroll
-    for (int c = 0; c < 2 * E; c++) p[c] = ok[c / 2] ? parent[x[c]] : x[c];
-    bool live[E];
-#pragma unroll
-    for (int i = 0; i < E; i++) {
-        live[i] = ok[i] && p[2 * i] != p[2 * i + 1];
-        if (!live[i]) {  // nothing to walk for this edge
-            p[2 * i] = x[2 * i];
-            p[2 * i + 1] = x[2 * i + 1];
+        for (int i = 0; i < E; i++) {
+            x[2 * i] = ok[i] ? u[i] : 0;
+            x[2 * i + 1] = ok[i] ? v[i] : 0;
         }
-    }
-    walk_split<2 * E>(parent, x, p, ds);
 #pragma unroll
-    for (int i = 0; i < E; i++)
-        if (live[i]) made += hook(parent, x[2 * i], x[2 * i + 1], ds);
-    return made;
+        for (int c = 0; c < 2 * E; c++) p[c] = ok[c / 2] ? parent[x[c]] : x[c];
+        bool live[E];
+#pragma unroll
+        for (int i = 0; i < E; i++) {
+            live[i] = ok[i] && p[2 * i] != p[2 * i + 1];
+            if (!live[i]) {  // nothing to walk for this edge
+                p[2 * i] = x[2 * i];
+                p[2 * i + 1] = x[2 * i + 1];
+            }
+        }
+        walk_split<2 * E>(parent, x, p, ds);
+#pragma unroll
+        for (int i = 0; i < E; i++)
+            if (live[i]) made += hook(parent, x[2 * i], x[2 * i + 1], ds);
+        return made;
+    }
 }
 
 // early: the first edges are read before the wait for the previous kernel
@@ -282,24 +301,10 @@ k_update_deep(int* __restrict__ parent, int n, const int* __restrict__ edges, in
 }
 
 template <int E>
-static int resident_blocks_deep(int block) {
-    static int cached[33] = {};
-    int& c = cached[block / 32];
-    if (!c) {
-        int per_sm = 0, dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_deep<E>, block, 0);
-        c = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-    }
-    return c;
-}
-
-template <int E>
 static void update_deep_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
                              int block, const cudaAccessPolicyWindow* window, int pdl, cudaStream_t s) {
     int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
-    const int64_t cap = resident_blocks_deep<E>(block);
+    const int64_t cap = resident_grid<k_update_deep<E>>(block);
     if (g > cap) g = cap;
     launch_windowed(k_update_deep<E>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k, vec, ds,
                     (int)(pdl == 2));
@@ -398,44 +403,21 @@ cudaError_t launch_update_split(int* parent, int n, const int* edges, int64_t k,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // pass 2 on a grid of resident CTAs, capped by the most it could have to do
-    static int per_sm[33] = {};
-    static int sms = 0;
-    int& ps = per_sm[cfg.block / 32];
-    if (!ps) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_update_live, cfg.block, 0);
-        if (ps < 1) ps = 1;
-        if (sms < 1) sms = 1;
-    }
     int64_t g = (k + 2LL * cfg.block - 1) / (2LL * cfg.block);
-    if (g > (int64_t)ps * sms) g = (int64_t)ps * sms;
+    const int64_t cap = resident_grid<k_update_live>(cfg.block);
+    if (g > cap) g = cap;
     launch_windowed(k_update_live, (unsigned)g, cfg.block, s, cfg.window, cfg.pdl != 0, parent,
                     (const int4*)live, (const unsigned*)count, sel, ds);
     return cudaGetLastError();
 }
 
-template <int E, int VARIANT>
-static int resident_blocks(int block) {
-    static int cached[33] = {};
-    int& c = cached[block / 32];
-    if (!c) {
-        int per_sm = 0, dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update<E, VARIANT>, block, 0);
-        c = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-    }
-    return c;
-}
 
 template <int E, int VARIANT>
 static void update_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
                         int block, const cudaAccessPolicyWindow* window, int pdl, cudaStream_t s) {
     int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
     if (VARIANT == 2) {
-        const int64_t cap = resident_blocks<E, VARIANT>(block);
+        const int64_t cap = resident_grid<k_update<E, VARIANT>>(block);
         if (g > cap) g = cap;
     }
     launch_windowed(k_update<E, VARIANT>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k, vec, ds,
@@ -623,15 +605,7 @@ static void query_one(unsigned g, int block, const cudaAccessPolicyWindow* windo
                       int* parent, int n, const int* pairs, int64_t k, int vec, uint8_t* out, int ovec,
                       DevState* ds) {
     if (PERSIST) {
-        static int cached[33] = {};
-        int& c = cached[block / 32];
-        if (!c) {
-            int per_sm = 0, dev = 0, sms = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_query<E, MODE, PERSIST>, block, 0);
-            c = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-        }
+        const int c = resident_grid<k_query<E, MODE, PERSIST>>(block);
         if (g > (unsigned)c) g = (unsigned)c;
     }
     launch_windowed(k_query<E, MODE, PERSIST>, g, block, s, window, pdl != 0, parent, n, pairs, k, vec, out, ovec,
