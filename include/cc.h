@@ -300,7 +300,12 @@ typedef struct {
 
 /* Start a server on `ctx` (a handle from cc_create). The server binds the
  * handle to its own compute stream until cc_server_destroy, and the caller
- * must not use the handle meanwhile. cfg may be NULL (defaults). */
+ * must not use the handle meanwhile. cfg may be NULL (defaults).
+ * Memory: besides the device staging ring, the server keeps one host record
+ * (about 64 bytes) per request it has ever been given, so that any ticket can
+ * be waited on and cc_server_latencies can report every request. A service
+ * that runs indefinitely bounds this by draining, destroying and re-creating
+ * the server from time to time (the forest is untouched by that). */
 cc_status cc_server_create(cc_ctx* ctx, const cc_server_config* cfg, cc_server** out);
 
 /* Enqueue one request; returns at once with a ticket (0, 1, 2, ... in arrival
