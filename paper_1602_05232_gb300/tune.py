@@ -228,6 +228,7 @@ WORKLOADS = {
     "segmented": lambda: ("segmented", I.segmented_workload()),
     "paper-random": lambda: ("plain", I.paper_stream("random", batch=10_000_000, q=1)),
     "paper-rmat5": lambda: ("plain", I.paper_stream("rmat5", batch=10_000_000, q=1)),
+    "paper-rmat16": lambda: ("plain", I.paper_stream("rmat16", batch=10_000_000, q=1)),
     "paper-3dgrid": lambda: ("plain", I.paper_stream("3dgrid", batch=10_000_000, q=1)),
 }
 
