@@ -594,6 +594,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int, dist) -> dict | None:
     gpu_launches = sum(la1[k] - la0[k] for k in la1)
     depth_max, depth_mean = f.depth()
     f.sync()
+    gather = gather_ceiling(f, d_pairs, qoff, B)
 
     total_ms_max = dist_max(dist, total_ms, dev)
     edges_all = dist_sum(dist, float(sum(edges_per_step)), dev)
@@ -626,6 +627,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int, dist) -> dict | None:
                 "bytes_per_unit": BYTES_PER_UNIT[dom],
                 "units_per_launch": per_launch_units,
                 "traffic": ncu_traffic(dom, args.workload)}
+    if gather:
+        gather["frac_of_peak"] = round(gather["GBps"] / peak, 4)
+        gather["dominant_kernel_frac_of_this"] = round(achieved / gather["GBps"], 4)
+        roofline["gather_ceiling"] = gather
 
     upd_ms = sum(kstats[k][1] for k in ("update", "compress_all", "compress_touched"))
     qry_ms = kstats["query"][1]
@@ -666,6 +671,42 @@ def run_gpu(args, rank: int, world: int, local_rank: int, dist) -> dict | None:
         "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu,
     }
     return out
+
+
+def gather_ceiling(f, d_pairs, qoff, B: int, reps: int = 20) -> dict | None:
+    """Context for the roofline: the query launch shape doing nothing but its
+    gathers. After a full compression every vertex points at its root, so a
+    query is decided by parent[u] == parent[v]: one streamed pair and two
+    random 4-byte reads, the minimum any update or query of this layout pays.
+    Timed with libcc's per-kernel events, like the kernels of the timed
+    regions, and run after them (it changes the forest)."""
+    import torch
+    if f.kernel_stats().get("query") is None:
+        return None
+    f.compress()                                # flat forest: parent equality decides
+    out = torch.empty(int(np.max(np.diff(qoff))), dtype=torch.uint8, device=d_pairs.device)
+    f.set_option("profile", 1)
+    f.sync()
+    f.kernel_stats(timing=True)                 # clears the timing sums
+    n0 = f.kernel_stats()["query"]
+    pairs = 0
+    for r in range(reps):
+        b = r % B
+        q = d_pairs[qoff[b]:qoff[b + 1]]
+        f.bulk_query(q, out=out[:q.shape[0]])
+        pairs += q.shape[0]
+    f.sync()
+    launches, ms = f.kernel_stats(timing=True)["query"]
+    f.set_option("profile", 0)
+    launches -= n0
+    if launches <= 0 or ms <= 0:
+        return None
+    us = 1e3 * ms / launches
+    gbps = BYTES_PER_UNIT["query"] * (pairs / launches) / (us * 1e-6) / 1e9
+    return {"kernel": "query on a flattened forest (parent equality only)", "us_per_launch": round(us, 3),
+            "GBps": round(gbps, 1), "launches": launches,
+            "what": "the same sector-model bytes per pair (73 B) moved by pure random gathers: the "
+                    "practical ceiling of this access pattern on this GPU, beside the copy-bandwidth peak"}
 
 
 def run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist) -> dict:
