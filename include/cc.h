@@ -126,7 +126,16 @@ typedef enum {
                                     before on the same stream does not write */
     CC_OPT_QUERY_PAIRS_PER_THREAD = 18, /* pairs per thread of the Bulk-Query kernel: 1, 2 or 4;
                                     0 = as CC_OPT_EDGES_PER_THREAD (default) */
-    CC_OPT__COUNT = 19
+    CC_OPT_HOOK = 19,            /* how the fused Bulk-Update links two roots: 0 = compare-and-swap on
+                                    the larger root, retried from its new root on failure (default);
+                                    1 = atomicMin on the larger root's parent word, and when that
+                                    word was no longer the root's own id, a join of the displaced
+                                    parent with the smaller root (cheaper when many edges of a
+                                    minibatch hook onto one root); 2 = as 1 for the first
+                                    Bulk-Update after cc_create or cc_reset (an empty forest,
+                                    where hub vertices make that contention worst), as 0 after.
+                                    Same answers and labels */
+    CC_OPT__COUNT = 20
 } cc_option;
 
 /* Kernel kinds reported by the launch counters and the profiler. */

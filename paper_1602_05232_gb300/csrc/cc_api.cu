@@ -51,7 +51,7 @@ struct DeviceScope {
 };
 
 const int64_t kDefaults[CC_OPT__COUNT] = {256, 2, 1, CC_COMPRESS_ALL, 0, 0, 0, 0,
-                                          512, 1, 65536, 1, 0, 0, 0, 0, 0, 1, 0};
+                                          512, 1, 65536, 1, 0, 0, 0, 0, 0, 1, 0, 0};
 
 }  // namespace
 
@@ -146,7 +146,7 @@ cc::Launch cfg_of(const cc_ctx* c) {
     return cc::Launch{(int)c->opt[CC_OPT_BLOCK], (int)c->opt[CC_OPT_EDGES_PER_THREAD],
                       (int)c->opt[CC_OPT_UPDATE_VARIANT], (int)c->opt[CC_OPT_QUERY_VARIANT],
                       c->window.num_bytes > 0 ? &c->window : nullptr, (int)c->opt[CC_OPT_PDL],
-                      (int)c->opt[CC_OPT_QUERY_PAIRS_PER_THREAD]};
+                      (int)c->opt[CC_OPT_QUERY_PAIRS_PER_THREAD], (int)(c->opt[CC_OPT_HOOK] == 1)};
 }
 
 cc_status check_pairs(const int32_t* p, int64_t k, const char* name) {
@@ -178,9 +178,17 @@ cc_status do_compress(cc_ctx* c, int scope, const int32_t* edges, int64_t k) {
     });
 }
 
+// Launch options of a Bulk-Update: CC_OPT_HOOK = 2 hooks with atomicMin only
+// for the first Bulk-Update on an empty forest (`first`), CAS afterwards.
+cc::Launch update_cfg(const cc_ctx* c, bool first) {
+    cc::Launch cfg = cfg_of(c);
+    if (c->opt[CC_OPT_HOOK] == 2) cfg.minhook = first ? 1 : 0;
+    return cfg;
+}
+
 // One Bulk-Update as a filter pass and a live-edge pass (update variant 4).
 // The list has room for k entries; growing it synchronises the stream once.
-cc_status split_update(cc_ctx* c, const int32_t* edges, int64_t k) {
+cc_status split_update(cc_ctx* c, const int32_t* edges, int64_t k, bool first) {
     cudaError_t e = cudaSuccess;
     if (!c->live_count) {
         e = cudaMalloc(&c->live_count, 2 * sizeof(unsigned));
@@ -206,7 +214,7 @@ cc_status split_update(cc_ctx* c, const int32_t* edges, int64_t k) {
     }
     const int sel = (int)(c->live_seq & 1u);
     cc_status s = run(c, CC_K_UPDATE, "bulk_update (two passes)", [&] {
-        return cc::launch_update_split(c->parent, (int)c->n, edges, k, c->ds, cfg_of(c), c->live,
+        return cc::launch_update_split(c->parent, (int)c->n, edges, k, c->ds, update_cfg(c, first), c->live,
                                        c->live_count, sel, c->stream);
     });
     if (s == CC_OK) {
@@ -469,14 +477,15 @@ cc_status cc_bulk_update(cc_ctx* c, const int32_t* edges, int64_t k) {
     CC_DEVICE(c);
     if (by_size(c) && c->opt[CC_OPT_UPDATE_SCHEDULE] != 1)
         return fail(CC_ERR_UNSUPPORTED, "union by size (CC_OPT_LINK = 1) needs CC_OPT_UPDATE_SCHEDULE = 1");
+    const bool first = c->fresh;  // the forest has no edge yet
     c->fresh = false;
     if (c->opt[CC_OPT_UPDATE_SCHEDULE] == 1) {
         s = paper_update(c, edges, k);
     } else if (c->opt[CC_OPT_UPDATE_VARIANT] == 4) {
-        s = split_update(c, edges, k);
+        s = split_update(c, edges, k, first);
     } else {
         s = run(c, CC_K_UPDATE, "bulk_update", [&] {
-            return cc::launch_update(c->parent, (int)c->n, edges, k, c->ds, cfg_of(c), c->stream);
+            return cc::launch_update(c->parent, (int)c->n, edges, k, c->ds, update_cfg(c, first), c->stream);
         });
     }
     if (s != CC_OK) return s;
@@ -844,6 +853,9 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
             break;
         case CC_OPT_PDL:
             if (value < 0 || value > 2) return fail(CC_ERR_ARG, "pdl %lld: need 0, 1 or 2", (long long)value);
+            break;
+        case CC_OPT_HOOK:
+            if (value < 0 || value > 2) return fail(CC_ERR_ARG, "hook %lld: need 0 (CAS), 1 (atomicMin) or 2 (atomicMin on an empty forest only)", (long long)value);
             break;
         case CC_OPT_QUERY_PAIRS_PER_THREAD:
             if (value != 0 && value != 1 && value != 2 && value != 4) return fail(CC_ERR_ARG, "query pairs per thread %lld: need 0, 1, 2 or 4", (long long)value);

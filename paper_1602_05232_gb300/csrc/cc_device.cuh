@@ -73,6 +73,40 @@ __device__ __forceinline__ int hook(int* parent, int ru, int rv, DevState* ds) {
     return 0;
 }
 
+// The same join with atomicMin instead of a compare-and-swap: parent[hi] is
+// lowered to lo (hi = the larger id). If hi was still a root, that is the
+// link. If not, its parent `old` comes back. When old > lo this call has just
+// moved hi's subtree from old's tree into lo's, and when old < lo it changed
+// nothing; either way the loop goes on joining old and lo, from their current
+// roots, which are both below hi -- so it ends, and old's tree is joined to
+// lo's, which keeps every earlier connection. Pointers only ever decrease, so
+// no cycle can form. A hook counts only a write at a root, so the number of
+// trees drops by exactly the links it returns. Under contention (many edges
+// of a minibatch on one hub root) every caller issues one atomic on the hub
+// and repairs elsewhere, where the CAS version fails, walks and retries in
+// rounds.
+static __device__ __noinline__ int hook_min(int* parent, int ru, int rv, DevState* ds) {
+    while (ru != rv) {
+        const int hi = ru > rv ? ru : rv;
+        const int lo = ru > rv ? rv : ru;
+        const int old = atomicMin(parent + hi, lo);
+        if (old == hi) return 1;
+        if (old > hi) {
+            flag(ds, ST_CORRUPT);
+            return 0;
+        }
+        if (old == lo) return 0;
+        ru = find_halving(parent, old, ds);
+        rv = find_halving(parent, lo, ds);
+    }
+    return 0;
+}
+
+// hook or hook_min, chosen per launch.
+__device__ __forceinline__ int hook_as(int* parent, int ru, int rv, DevState* ds, int minhook) {
+    return minhook ? hook_min(parent, ru, rv, ds) : hook(parent, ru, rv, ds);
+}
+
 // Walk W chains to their roots in lockstep with path splitting. Chain c is at
 // node x[c] whose parent p[c] has been read; it is finished when p[c] >= x[c]
 // (p == x: x is the root). Each round reads the grandparent of every

@@ -35,6 +35,7 @@ struct Launch {
     const cudaAccessPolicyWindow* window = nullptr;  // L2 window over the forest, or none
     int pdl = 0;  // programmatic dependent launch: 0 off, 1 wait first, 2 first pairs before the wait
     int qept = 0; // pairs per thread of the query kernel (0 = ept)
+    int minhook = 0;  // 1: Bulk-Update hooks with atomicMin + repair (hook_min) instead of CAS
 };
 
 // Alignment class of a pair array: 2 = 16-byte, 1 = 8-byte, 0 = 4-byte.

@@ -106,7 +106,7 @@ cudaError_t launch_reset(int* parent, int64_t n, int block, cudaStream_t s) {
 template <int E, int VARIANT>
 __device__ __forceinline__ int update_edges(int* __restrict__ parent, int n,
                                             const int (&u)[E], const int (&v)[E], int64_t e0,
-                                            int64_t k, DevState* __restrict__ ds) {
+                                            int64_t k, DevState* __restrict__ ds, int minhook) {
     bool ok[E];
     bool bad = false;
     int made = 0;
@@ -131,7 +131,7 @@ __device__ __forceinline__ int update_edges(int* __restrict__ parent, int n,
             if (!ok[i] || pu[i] == pv[i]) continue;
             int ru = pu[i] == u[i] ? u[i] : find_from(parent, u[i], pu[i], ds);
             int rv = pv[i] == v[i] ? v[i] : find_from(parent, v[i], pv[i], ds);
-            made += hook(parent, ru, rv, ds);
+            made += hook_as(parent, ru, rv, ds, minhook);
         }
         return made;
     } else {
@@ -156,7 +156,7 @@ __device__ __forceinline__ int update_edges(int* __restrict__ parent, int n,
         walk_split<2 * E>(parent, x, p, ds);
 #pragma unroll
         for (int i = 0; i < E; i++)
-            if (live[i]) made += hook(parent, x[2 * i], x[2 * i + 1], ds);
+            if (live[i]) made += hook_as(parent, x[2 * i], x[2 * i + 1], ds, minhook);
         return made;
     }
 }
@@ -166,7 +166,7 @@ __device__ __forceinline__ int update_edges(int* __restrict__ parent, int n,
 template <int E, int VARIANT>
 __global__ void __launch_bounds__(1024)
 k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
-         DevState* __restrict__ ds, int early) {
+         DevState* __restrict__ ds, int early, int minhook) {
     pdl_trigger();
     if (!early) pdl_wait();
     int made = 0;
@@ -176,7 +176,7 @@ k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t
             int u[E], v[E];
             load_pairs<E>(edges, e0, k, vec, u, v);
             if (early) pdl_wait();
-            made = update_edges<E, VARIANT>(parent, n, u, v, e0, k, ds);
+            made = update_edges<E, VARIANT>(parent, n, u, v, e0, k, ds, minhook);
         }
     } else {
         // persistent grid: loop over chunks, loading the next chunk's edges
@@ -189,7 +189,7 @@ k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t
             const int64_t nx = e0 + stride;
             int nu[E] = {}, nv[E] = {};
             if (nx < k) load_pairs<E>(edges, nx, k, vec, nu, nv);
-            made += update_edges<E, 1>(parent, n, u, v, e0, k, ds);
+            made += update_edges<E, 1>(parent, n, u, v, e0, k, ds, minhook);
 #pragma unroll
             for (int i = 0; i < E; i++) {
                 u[i] = nu[i];
@@ -241,7 +241,8 @@ __device__ __forceinline__ void gather_parents(const int* parent, unsigned m, co
 // current root, and equal values still prove the endpoints joined.
 template <int E>
 __device__ __forceinline__ int walk_and_hook(int* parent, unsigned m, const int (&u)[E], const int (&v)[E],
-                                             const int (&pu)[E], const int (&pv)[E], DevState* ds) {
+                                             const int (&pu)[E], const int (&pv)[E], DevState* ds,
+                                             int minhook) {
     int x[2 * E], p[2 * E];
     bool live[E];
 #pragma unroll
@@ -256,7 +257,7 @@ __device__ __forceinline__ int walk_and_hook(int* parent, unsigned m, const int 
     int made = 0;
 #pragma unroll
     for (int i = 0; i < E; i++)
-        if (live[i]) made += hook(parent, x[2 * i], x[2 * i + 1], ds);
+        if (live[i]) made += hook_as(parent, x[2 * i], x[2 * i + 1], ds, minhook);
     return made;
 }
 
@@ -267,7 +268,7 @@ __device__ __forceinline__ int walk_and_hook(int* parent, unsigned m, const int 
 template <int E>
 __global__ void __launch_bounds__(1024)
 k_update_deep(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
-              DevState* __restrict__ ds, int early) {
+              DevState* __restrict__ ds, int early, int minhook) {
     pdl_trigger();
     if (!early) pdl_wait();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * E;
@@ -287,7 +288,7 @@ k_update_deep(int* __restrict__ parent, int n, const int* __restrict__ edges, in
         gather_parents<E>(parent, m1, u1, v1, pu1, pv1);
         int u2[E] = {}, v2[E] = {};
         if (e2 < k) load_pairs<E>(edges, e2, k, vec, u2, v2);
-        made += walk_and_hook<E>(parent, m0, u0, v0, pu0, pv0, ds);
+        made += walk_and_hook<E>(parent, m0, u0, v0, pu0, pv0, ds, minhook);
 #pragma unroll
         for (int i = 0; i < E; i++) {
             u0[i] = u1[i]; v0[i] = v1[i]; pu0[i] = pu1[i]; pv0[i] = pv1[i];
@@ -302,12 +303,13 @@ k_update_deep(int* __restrict__ parent, int n, const int* __restrict__ edges, in
 
 template <int E>
 static void update_deep_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
-                             int block, const cudaAccessPolicyWindow* window, int pdl, cudaStream_t s) {
+                             int block, const cudaAccessPolicyWindow* window, int pdl, int minhook,
+                             cudaStream_t s) {
     int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
     const int64_t cap = resident_grid<k_update_deep<E>>(block);
     if (g > cap) g = cap;
     launch_windowed(k_update_deep<E>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k, vec, ds,
-                    (int)(pdl == 2));
+                    (int)(pdl == 2), minhook);
 }
 
 // --- VARIANT 4: filter pass + live-edge pass ------------------------------
@@ -364,7 +366,7 @@ k_update_filter(const int* __restrict__ parent, int n, const int* __restrict__ e
 // Pass 2: two listed edges per thread per step, their four walks in lockstep.
 __global__ void __launch_bounds__(1024)
 k_update_live(int* __restrict__ parent, const int4* __restrict__ live, const unsigned* __restrict__ count,
-              int sel, DevState* __restrict__ ds) {
+              int sel, DevState* __restrict__ ds, int minhook) {
     pdl_trigger();
     pdl_wait();
     const int64_t m = count[sel];
@@ -375,7 +377,7 @@ k_update_live(int* __restrict__ parent, const int4* __restrict__ live, const uns
         const int4 b = i + 1 < m ? live[i + 1] : a;
         const unsigned on = i + 1 < m ? 3u : 1u;
         const int u[2] = {a.x, b.x}, v[2] = {a.y, b.y}, pu[2] = {a.z, b.z}, pv[2] = {a.w, b.w};
-        made += walk_and_hook<2>(parent, on, u, v, pu, pv, ds);
+        made += walk_and_hook<2>(parent, on, u, v, pu, pv, ds, minhook);
     }
     made = __reduce_add_sync(0xffffffffu, made);
     if ((threadIdx.x & 31) == 0 && made) atomicAdd(&ds->unions, (unsigned long long)made);
@@ -407,28 +409,29 @@ cudaError_t launch_update_split(int* parent, int n, const int* edges, int64_t k,
     const int64_t cap = resident_grid<k_update_live>(cfg.block);
     if (g > cap) g = cap;
     launch_windowed(k_update_live, (unsigned)g, cfg.block, s, cfg.window, cfg.pdl != 0, parent,
-                    (const int4*)live, (const unsigned*)count, sel, ds);
+                    (const int4*)live, (const unsigned*)count, sel, ds, cfg.minhook);
     return cudaGetLastError();
 }
 
 
 template <int E, int VARIANT>
 static void update_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
-                        int block, const cudaAccessPolicyWindow* window, int pdl, cudaStream_t s) {
+                        int block, const cudaAccessPolicyWindow* window, int pdl, int minhook,
+                        cudaStream_t s) {
     int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
     if (VARIANT == 2) {
         const int64_t cap = resident_grid<k_update<E, VARIANT>>(block);
         if (g > cap) g = cap;
     }
     launch_windowed(k_update<E, VARIANT>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k, vec, ds,
-                    (int)(pdl == 2));
+                    (int)(pdl == 2), minhook);
 }
 
 cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevState* ds,
                           Launch cfg, cudaStream_t s) {
     if (k <= 0) return cudaSuccess;
     const int vec = pair_vec(edges);
-#define CC_UPD(E, V) update_inst<E, V>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, s)
+#define CC_UPD(E, V) update_inst<E, V>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, s)
     switch (cfg.variant * 8 + cfg.ept) {
         case 1: CC_UPD(1, 0); break;
         case 2: CC_UPD(2, 0); break;
@@ -439,9 +442,9 @@ cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevSt
         case 17: CC_UPD(1, 2); break;
         case 18: CC_UPD(2, 2); break;
         case 20: CC_UPD(4, 2); break;
-        case 25: update_deep_inst<1>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, s); break;
-        case 26: update_deep_inst<2>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, s); break;
-        case 28: update_deep_inst<4>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, s); break;
+        case 25: update_deep_inst<1>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, s); break;
+        case 26: update_deep_inst<2>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, s); break;
+        case 28: update_deep_inst<4>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, s); break;
         default: return cudaErrorInvalidValue;
     }
 #undef CC_UPD

@@ -37,6 +37,13 @@ OPTION_SETS = {
     "splitting_query": {"query_halving": 2, "compress_every": 0, "edges_per_thread": 4},
     "splitting_query_persistent": {"query_halving": 2, "compress_every": 0, "query_variant": 1},
     "pdl_off": {"pdl": 0},
+    "min_hook": {"hook": 1},
+    "min_hook_persistent": {"hook": 1, "update_variant": 2, "edges_per_thread": 4, "compress_every": 0},
+    "min_hook_deep": {"hook": 1, "update_variant": 3, "edges_per_thread": 2, "block": 128, "compress_every": 0,
+                      "query_pairs_per_thread": 2, "l2_persist": 1},
+    "min_hook_two_pass": {"hook": 1, "update_variant": 4, "edges_per_thread": 1, "compress_every": 3},
+    "min_hook_first_only": {"hook": 2, "update_variant": 3, "edges_per_thread": 2, "compress_every": 0},
+    "min_hook_first_only_two_pass": {"hook": 2, "update_variant": 4, "edges_per_thread": 2, "compress_every": 0},
     "two_pass_ept4": {"update_variant": 4, "edges_per_thread": 4, "compress_every": 0},
     "two_pass_ept1_pdl0": {"update_variant": 4, "edges_per_thread": 1, "pdl": 0, "compress_every": 2},
     "two_pass_ept2_pdl2_b1024": {"update_variant": 4, "edges_per_thread": 2, "pdl": 2, "block": 1024,
@@ -108,7 +115,8 @@ def test_uniform_small_every_batch(cc, opts):
 @pytest.mark.parametrize("opts", ["default", "ept1_b64", "no_compress", "touched_compress",
                                   "lockstep_ept4_nocompress", "persistent_ept4",
                                   "persistent_query_halving", "splitting_query", "deep_prefetch_ept2_pdl2",
-                                  "two_pass_ept4", "query_ept2_update_ept4"])
+                                  "two_pass_ept4", "query_ept2_update_ept4", "min_hook", "min_hook_persistent",
+                                  "min_hook_deep", "min_hook_two_pass", "min_hook_first_only"])
 def test_rmat_small(cc, opts):
     s = I.rmat_stream(scale=16, m=1 << 20, batch=(1 << 16) + 3, q=(1 << 16) - 5, seed=1)
     run_stream(cc, s, OPTION_SETS[opts], label_every=4, check_invariants=True)
@@ -116,7 +124,8 @@ def test_rmat_small(cc, opts):
 
 @pytest.mark.parametrize("opts", ["default", "no_compress", "ept4_b1024", "compress_every3",
                                   "lockstep", "persistent_ept1_b1024", "splitting_query",
-                                  "deep_prefetch_ept1_b1024", "two_pass_ept1_pdl0"])
+                                  "deep_prefetch_ept1_b1024", "two_pass_ept1_pdl0", "min_hook",
+                                  "min_hook_deep"])
 def test_grid_small(cc, opts):
     s = I.grid_stream(512, 512, batch=(1 << 14) + 1, q=1 << 14, seed=2)
     ref = run_stream(cc, s, OPTION_SETS[opts], label_every=8, check_invariants=True)
