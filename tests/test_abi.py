@@ -61,3 +61,15 @@ def test_product_path_fails_loudly_without_the_library(tmp_path):
     from paper_1602_05232_gb300 import cc
     with pytest.raises(RuntimeError, match="libcc.so not found"):
         cc.load(tmp_path / "libcc.so")
+
+
+def test_binding_option_numbers_match_the_header():
+    """cc.OPTIONS names every CC_OPT_* of include/cc.h with the header's number."""
+    from paper_1602_05232_gb300 import cc
+    text = re.sub(r"/\*.*?\*/", "", (ROOT / "include" / "cc.h").read_text(), flags=re.S)
+    body = re.search(r"typedef enum \{([^}]*)\}\s*cc_option;", text).group(1)
+    enum = {m.group(1).lower(): int(m.group(2))
+            for m in re.finditer(r"\bCC_OPT_(\w+)\s*=\s*(\d+)", body) if m.group(1) != "_COUNT"}
+    count = int(re.search(r"\bCC_OPT__COUNT\s*=\s*(\d+)", body).group(1))
+    assert sorted(enum.values()) == list(range(count))
+    assert enum == cc.OPTIONS

@@ -214,6 +214,39 @@ def test_argument_errors_leave_state(cc):
     assert f.components() == 10
 
 
+# (option, rejected values, accepted values): include/cc.h gives the ranges
+OPTION_RANGES = [
+    ("block", [0, 63, 100, 1056], [64, 1024]),
+    ("edges_per_thread", [0, 3, 8], [1, 2, 4]),
+    ("compress_every", [-1], [0, 16]),
+    ("compress_scope", [2, -1], [0, 1]),
+    ("query_halving", [-1, 3], [0, 1, 2]),
+    ("profile", [2], [0, 1]),
+    ("update_variant", [-1, 5], [0, 1, 2, 3, 4]),
+    ("query_variant", [2], [0, 1]),
+    ("pdl", [-1, 3], [0, 1, 2]),
+    ("query_pairs_per_thread", [3, 8], [0, 1, 2, 4]),
+    ("hook", [-1, 3], [0, 1, 2]),
+    ("bulk_find", [2], [0, 1]),
+    ("update_schedule", [2], [0, 1]),
+]
+
+
+@pytest.mark.parametrize("name,bad,good", OPTION_RANGES, ids=[o[0] for o in OPTION_RANGES])
+def test_option_ranges(cc, name, bad, good):
+    f = cc.Forest(100)
+    before = f.get_option(name)
+    for v in bad:
+        with pytest.raises(cc.CCError) as ex:
+            f.set_option(name, v)
+        assert ex.value.status == cc.CC_ERR_ARG
+        assert f.get_option(name) == before          # a rejected value changes nothing
+    for v in good:
+        f.set_option(name, v)
+        assert f.get_option(name) == v
+    f.close()
+
+
 def test_checkpoint_resume(cc):
     s = I.rmat_stream(scale=14, m=1 << 17, batch=1 << 13, q=1 << 12, seed=4)
     whole = cc.Forest(s.n)
