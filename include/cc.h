@@ -327,6 +327,19 @@ cc_status cc_server_create(cc_ctx* ctx, const cc_server_config* cfg, cc_server**
 cc_status cc_server_enqueue(cc_server* s, int32_t kind, const int32_t* data, int64_t k,
                             uint8_t* out, uint64_t* ticket);
 
+/* Enqueue n requests in array order, as n calls of cc_server_enqueue would,
+ * but under one lock and with one wake-up of the worker: for callers that
+ * receive requests in batches (a network front end draining a socket, a
+ * replayed trace), where a call per request would cost more than the request.
+ * Request i is (kinds[i], data[i], k[i], out[i]) with the meaning and
+ * ownership of cc_server_enqueue; `out` may be NULL when no request is a
+ * query, and out[i] is ignored for updates. Its ticket is *first_ticket + i.
+ * All n are checked before any is accepted: on an argument error nothing is
+ * enqueued (CC_ERR_ARG, naming the first bad index). */
+cc_status cc_server_enqueue_many(cc_server* s, int64_t n, const int32_t* kinds,
+                                 const int32_t* const* data, const int64_t* k, uint8_t* const* out,
+                                 uint64_t* first_ticket);
+
 /* Block until request `ticket` completes; *latency_s (may be NULL) receives
  * its enqueue-to-completion time in seconds. */
 cc_status cc_server_wait(cc_server* s, uint64_t ticket, double* latency_s);

@@ -82,6 +82,7 @@ def load(path: str | Path | None = None) -> ctypes.CDLL:
         "cc_submit": [vp, vp, i64],
         "cc_server_create": [vp, vp, ctypes.POINTER(ctypes.c_void_p)],
         "cc_server_enqueue": [vp, i32, vp, i64, vp, ctypes.POINTER(ctypes.c_uint64)],
+        "cc_server_enqueue_many": [vp, i64, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_uint64)],
         "cc_server_wait": [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)],
         "cc_server_drain": [vp],
         "cc_server_get_stats": [vp, vp],
@@ -369,6 +370,47 @@ class Server:
               self._L)
         self._keep[t.value] = (data, out)   # keep the buffers alive until drained
         return t.value
+
+    def enqueue_many(self, kinds: np.ndarray, data_ptrs: np.ndarray, ks: np.ndarray,
+                     out_ptrs: np.ndarray | None = None, keep=None) -> int:
+        """n requests in one call (cc_server_enqueue_many): int32 kinds, uint64
+        host addresses of the int32 (k, 2) data, int64 k (pairs), and uint64
+        host addresses of the uint8 outputs (0 for updates). The caller keeps
+        the buffers alive until the requests complete (or passes them in
+        `keep`). Returns the first ticket; request i has ticket first + i."""
+        kinds = np.ascontiguousarray(kinds, dtype=np.int32)
+        data_ptrs = np.ascontiguousarray(data_ptrs, dtype=np.uint64)
+        ks = np.ascontiguousarray(ks, dtype=np.int64)
+        n = len(kinds)
+        if len(data_ptrs) != n or len(ks) != n or (out_ptrs is not None and len(out_ptrs) != n):
+            raise ValueError("enqueue_many: arrays of different lengths")
+        optr = None
+        if out_ptrs is not None:
+            out_ptrs = np.ascontiguousarray(out_ptrs, dtype=np.uint64)
+            optr = out_ptrs.ctypes.data
+        t = ctypes.c_uint64()
+        check(self._L.cc_server_enqueue_many(self._h, n, kinds.ctypes.data, data_ptrs.ctypes.data,
+                                             ks.ctypes.data, optr, ctypes.byref(t)), self._L)
+        if keep is not None:
+            self._keep[t.value] = keep
+        return t.value
+
+    def enqueue_list(self, requests) -> int:
+        """[(kind, data, out)] as for enqueue, in one call; returns the first ticket."""
+        kinds, dp, ks, op = [], [], [], []
+        for kind, data, out in requests:
+            if data.is_cuda or data.dtype != torch.int32 or not data.is_contiguous():
+                raise TypeError("data: expected a contiguous host int32 tensor")
+            k = data.numel() // 2
+            if kind == OP_QUERY and (out is None or out.is_cuda or out.dtype != torch.uint8
+                                     or out.numel() < k):
+                raise TypeError("out: expected a host uint8 tensor of k elements")
+            kinds.append(kind)
+            dp.append(data.data_ptr())
+            ks.append(k)
+            op.append(out.data_ptr() if kind == OP_QUERY else 0)
+        return self.enqueue_many(np.array(kinds), np.array(dp, dtype=np.uint64), np.array(ks),
+                                 np.array(op, dtype=np.uint64), keep=list(requests))
 
     def wait(self, ticket: int) -> float:
         lat = ctypes.c_double()

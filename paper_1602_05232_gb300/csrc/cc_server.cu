@@ -21,6 +21,7 @@
 
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -370,6 +371,43 @@ cc_status cc_server_enqueue(cc_server* s, int32_t kind, const int32_t* data, int
     if (kind == CC_OP_UPDATE) { s->n_upd++; s->edges += k; } else { s->n_qry++; s->pairs += k; }
     if (ticket) *ticket = (uint64_t)(s->reqs.size() - 1);
     s->cv_work.notify_one();
+    return CC_OK;
+}
+
+cc_status cc_server_enqueue_many(cc_server* s, int64_t n, const int32_t* kinds,
+                                 const int32_t* const* data, const int64_t* k, uint8_t* const* out,
+                                 uint64_t* first_ticket) {
+    if (!s) return server_fail(CC_ERR_ARG, "cc_server_enqueue_many: null server");
+    if (n < 0) return server_fail(CC_ERR_ARG, "cc_server_enqueue_many: n < 0");
+    if (n > 0 && (!kinds || !data || !k)) return server_fail(CC_ERR_ARG, "cc_server_enqueue_many: null array");
+    char msg[160];
+    for (int64_t i = 0; i < n; i++) {  // everything is checked before anything is accepted
+        const char* why = nullptr;
+        if (kinds[i] != CC_OP_UPDATE && kinds[i] != CC_OP_QUERY) why = "unknown kind";
+        else if (k[i] < 0 || k[i] > s->cap || k[i] > INT32_MAX) why = "k out of range (larger than the staging ring?)";
+        else if (k[i] > 0 && !data[i]) why = "null data";
+        else if (k[i] > 0 && kinds[i] == CC_OP_QUERY && (!out || !out[i])) why = "null out for a query";
+        if (why) {
+            snprintf(msg, sizeof msg, "cc_server_enqueue_many: request %lld: %s", (long long)i, why);
+            return server_fail(CC_ERR_ARG, msg);
+        }
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->err != CC_OK) return server_fail(s->err, s->errmsg.c_str());
+    if (s->stop) return server_fail(CC_ERR_ARG, "cc_server_enqueue_many: server is stopping");
+    const double t = now_s();
+    if (first_ticket) *first_ticket = (uint64_t)s->reqs.size();
+    for (int64_t i = 0; i < n; i++) {
+        Req r;
+        r.kind = kinds[i];
+        r.data = data[i];
+        r.k = k[i];
+        r.out = kinds[i] == CC_OP_QUERY ? out[i] : nullptr;
+        r.t_arrive = t;
+        s->reqs.push_back(r);
+        if (r.kind == CC_OP_UPDATE) { s->n_upd++; s->edges += r.k; } else { s->n_qry++; s->pairs += r.k; }
+    }
+    if (n > 0) s->cv_work.notify_one();
     return CC_OK;
 }
 

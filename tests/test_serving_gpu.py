@@ -52,11 +52,13 @@ def alone_answers(n, reqs, data):
     return want, uf.labels()
 
 
-def serve(cc, n, reqs, data, paced=False, **cfg):
+def serve(cc, n, reqs, data, paced=False, batch=0, **cfg):
+    """batch > 0: hand the requests over `batch` at a time (cc_server_enqueue_many)."""
     f = cc.Forest(n)
     outs = {}
     with cc.Server(f, **cfg) as srv:
         t0 = time.perf_counter()
+        pending = []
         for i, (r, d) in enumerate(zip(reqs, data)):
             if paced:
                 while time.perf_counter() - t0 < r.t:
@@ -65,7 +67,15 @@ def serve(cc, n, reqs, data, paced=False, **cfg):
             if r.kind == 1:
                 out = torch.zeros(r.size, dtype=torch.uint8).pin_memory()
                 outs[i] = out
-            srv.enqueue(r.kind, d, out)
+            if batch:
+                pending.append((r.kind, d, out))
+                if len(pending) == batch:
+                    assert srv.enqueue_list(pending) == i + 1 - batch   # consecutive tickets
+                    pending = []
+            else:
+                srv.enqueue(r.kind, d, out)
+        if pending:
+            srv.enqueue_list(pending)
         srv.drain()
         lat = srv.latencies()
         st = srv.stats()
@@ -74,7 +84,7 @@ def serve(cc, n, reqs, data, paced=False, **cfg):
     return {i: o.numpy() for i, o in outs.items()}, labels, lat, st
 
 
-@pytest.mark.parametrize("mode", ["burst", "paced", "no_merge", "tiny_ring"])
+@pytest.mark.parametrize("mode", ["burst", "paced", "no_merge", "tiny_ring", "batched_enqueue"])
 def test_served_equals_alone(cc, mode):
     n, reqs, data = make_trace(scale=16, m=1 << 19, seed=7)
     want, want_labels = alone_answers(n, reqs, data)
@@ -83,7 +93,8 @@ def test_served_equals_alone(cc, mode):
         cfg = {"merge": False}
     if mode == "tiny_ring":
         cfg = {"ring_pairs": 1 << 12, "max_group_pairs": 1 << 11}
-    got, labels, lat, st = serve(cc, n, reqs, data, paced=(mode == "paced"), **cfg)
+    got, labels, lat, st = serve(cc, n, reqs, data, paced=(mode == "paced"),
+                                 batch=(97 if mode == "batched_enqueue" else 0), **cfg)
     for i, w in want.items():
         assert np.array_equal(got[i], w), f"request {i} differs from running it alone"
     assert np.array_equal(labels, want_labels)
@@ -153,3 +164,27 @@ def test_server_errors(cc):
     # the handle is usable again after the server is gone
     f.bulk_update(torch.tensor([[1, 2]], dtype=torch.int32, device="cuda"))
     assert f.components() == 99
+
+
+def test_enqueue_many_checks_everything_first(cc):
+    f = cc.Forest(100)
+    e = torch.tensor([[1, 2], [3, 4]], dtype=torch.int32).pin_memory()
+    q = torch.tensor([[1, 2]], dtype=torch.int32).pin_memory()
+    o = torch.zeros(1, dtype=torch.uint8).pin_memory()
+    with cc.Server(f) as srv:
+        kinds = np.array([cc.OP_UPDATE, cc.OP_QUERY, 7], dtype=np.int32)     # request 2: bad kind
+        ptrs = np.array([e.data_ptr(), q.data_ptr(), e.data_ptr()], dtype=np.uint64)
+        ks = np.array([2, 1, 2], dtype=np.int64)
+        outs = np.array([0, o.data_ptr(), 0], dtype=np.uint64)
+        with pytest.raises(cc.CCError) as ex:
+            srv.enqueue_many(kinds, ptrs, ks, outs)
+        assert ex.value.status == cc.CC_ERR_ARG and "request 2" in str(ex.value)
+        assert srv.stats()["requests"] == 0                    # nothing was accepted
+        with pytest.raises(cc.CCError):                        # a query without an output
+            srv.enqueue_many(kinds[:2], ptrs[:2], ks[:2], None)
+        assert srv.stats()["requests"] == 0
+        first = srv.enqueue_many(kinds[:2], ptrs[:2], ks[:2], outs[:2], keep=(e, q, o))
+        assert first == 0
+        srv.drain()
+        assert srv.stats()["completed"] == 2 and o[0] == 1     # 1-2 joined by the update before it
+    f.close()
