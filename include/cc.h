@@ -135,7 +135,13 @@ typedef enum {
                                     Bulk-Update after cc_create or cc_reset (an empty forest,
                                     where hub vertices make that contention worst), as 0 after.
                                     Same answers and labels */
-    CC_OPT__COUNT = 20
+    CC_OPT_SV_GRAPH = 20,        /* CC_OPT_UPDATE_SCHEDULE = 1 only: 1 = its hooking rounds run as one
+                                    CUDA graph whose while node repeats them on the device until a
+                                    round hooks nothing, with no host round trip (default); the
+                                    graph is built on the first such update and rebuilt when the A''
+                                    buffer grows or the block size changes. 0 = the host reads a
+                                    flag after every round. Same answers and labels */
+    CC_OPT__COUNT = 21
 } cc_option;
 
 /* Kernel kinds reported by the launch counters and the profiler. */

@@ -51,7 +51,7 @@ struct DeviceScope {
 };
 
 const int64_t kDefaults[CC_OPT__COUNT] = {256, 2, 1, CC_COMPRESS_ALL, 0, 0, 0, 0,
-                                          512, 1, 65536, 1, 0, 0, 0, 0, 0, 1, 0, 0};
+                                          512, 1, 65536, 1, 0, 0, 0, 0, 0, 1, 0, 0, 1};
 
 }  // namespace
 
@@ -90,7 +90,11 @@ struct cc_ctx {
     int* a2 = nullptr;            // A'': compacted pairs of distinct roots
     int64_t a2_cap = 0;           // in pairs
     int* comp = nullptr;          // component labels of A'' endpoints (n entries)
-    unsigned* pcount = nullptr;   // device: [0] = |A''|, [1] = hooked flag
+    unsigned* pcount = nullptr;   // device: [0] = |A''|, [1] = hooked flag, [2] = rounds (graph)
+    cudaGraphExec_t sv_exec = nullptr;  // the hooking rounds as one graph (CC_OPT_SV_GRAPH)
+    const int* sv_a2 = nullptr;         // ... built for this A'' buffer,
+    int sv_grid = 0, sv_block = 0;      // ... and this launch shape
+    bool stats_on_device = false;       // last_nonloop / last_rounds still to be read from pcount
     int64_t last_nonloop = 0;
     int32_t last_rounds = 0;
 
@@ -224,12 +228,60 @@ cc_status split_update(cc_ctx* c, const int32_t* edges, int64_t k, bool first) {
     return s;
 }
 
+// Steps 2-3 of the paper's schedule without a host round trip: the hooking
+// rounds as one graph launch (build_sv_loop), then the join, on a grid of 8
+// CTAs per SM (the kernels stride over A'', whose size they read on the
+// device). |A''| and the round count stay on the device until asked for.
+cc_status paper_rounds_graph(cc_ctx* c, int block) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    const int grid = 8 * (sms > 0 ? sms : 1);
+    if (!c->sv_exec || c->sv_a2 != c->a2 || c->sv_grid != grid || c->sv_block != block) {
+        if (c->sv_exec) cudaGraphExecDestroy(c->sv_exec);
+        c->sv_exec = nullptr;
+        cudaError_t e = cc::build_sv_loop(c->a2, c->pcount, c->comp, c->ds, grid, block, &c->sv_exec);
+        if (e != cudaSuccess) return cuda_fail(e, "schedule 1: building the rounds graph");
+        c->sv_a2 = c->a2;
+        c->sv_grid = grid;
+        c->sv_block = block;
+    }
+    cc_status st = run(c, CC_K_UPDATE, "schedule 1: components rounds (graph)", [&] {
+        return cudaGraphLaunch(c->sv_exec, c->stream);
+    });
+    if (st != CC_OK) return st;
+    c->stats_on_device = true;
+    if (c->opt[CC_OPT_LINK] == 1) {
+        c->launches[CC_K_UPDATE]++;  // vote, then join
+        return run(c, CC_K_UPDATE, "schedule 1: size join", [&] {
+            return cc::launch_size_join(c->a2, c->pcount, c->comp, c->parent, c->size, c->best, c->ds,
+                                        grid, block, c->stream);
+        });
+    }
+    return run(c, CC_K_UPDATE, "schedule 1: join", [&] {
+        return cc::launch_join(c->a2, c->pcount, c->comp, c->parent, c->ds, grid, block, c->stream);
+    });
+}
+
+// The last update's |A''| and round count, from the device when the rounds
+// ran as a graph. Synchronises the stream in that case.
+cc_status refresh_schedule_stats(cc_ctx* c) {
+    if (!c->stats_on_device) return CC_OK;
+    unsigned h[3] = {0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, c->pcount, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "schedule 1: reading the round statistics");
+    c->last_nonloop = h[0];
+    c->last_rounds = (int32_t)h[2];
+    c->stats_on_device = false;
+    return CC_OK;
+}
+
 // Algorithm 2 as written, one Bulk-Update: relabel + filter, CC rounds, join.
 cc_status paper_update(cc_ctx* c, const int32_t* edges, int64_t k) {
     cudaError_t e = cudaSuccess;
     if (!c->comp) {
         e = cudaMalloc(&c->comp, sizeof(int) * (size_t)c->n);
-        if (e == cudaSuccess) e = cudaMalloc(&c->pcount, 2 * sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMalloc(&c->pcount, 4 * sizeof(unsigned));
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(CC_ERR_OOM, "schedule 1: component array of %lld entries", (long long)c->n);
@@ -275,6 +327,8 @@ cc_status paper_update(cc_ctx* c, const int32_t* edges, int64_t k) {
         return cc::launch_relabel(c->parent, (int)c->n, edges, k, c->a2, c->pcount, c->comp, c->ds, block, c->stream);
     });
     if (st != CC_OK) return st;
+    if (c->opt[CC_OPT_SV_GRAPH] == 1) return paper_rounds_graph(c, block);
+    c->stats_on_device = false;
     unsigned m2 = 0;
     e = cudaMemcpyAsync(&m2, c->pcount, sizeof m2, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -413,6 +467,7 @@ cc_status cc_destroy(cc_ctx* c) {
         cudaFree(c->a2);
         cudaFree(c->comp);
         cudaFree(c->pcount);
+        if (c->sv_exec) cudaGraphExecDestroy(c->sv_exec);
         cudaFree(c->size);
         cudaFree(c->best);
         cudaFree(c->live);
@@ -854,6 +909,9 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
         case CC_OPT_PDL:
             if (value < 0 || value > 2) return fail(CC_ERR_ARG, "pdl %lld: need 0, 1 or 2", (long long)value);
             break;
+        case CC_OPT_SV_GRAPH:
+            if (value != 0 && value != 1) return fail(CC_ERR_ARG, "option %d takes 0 or 1", option);
+            break;
         case CC_OPT_HOOK:
             if (value < 0 || value > 2) return fail(CC_ERR_ARG, "hook %lld: need 0 (CAS), 1 (atomicMin) or 2 (atomicMin on an empty forest only)", (long long)value);
             break;
@@ -964,6 +1022,11 @@ int64_t cc_num_vertices(const cc_ctx* c) { return c ? c->n : 0; }
 
 cc_status cc_schedule_stats(cc_ctx* c, int64_t* nonloop_edges, int32_t* rounds) {
     CC_CHECK_CTX(c);
+    {
+        CC_DEVICE(c);
+        cc_status st = refresh_schedule_stats(c);
+        if (st != CC_OK) return st;
+    }
     if (nonloop_edges) *nonloop_edges = c->last_nonloop;
     if (rounds) *rounds = c->last_rounds;
     return CC_OK;
@@ -971,6 +1034,11 @@ cc_status cc_schedule_stats(cc_ctx* c, int64_t* nonloop_edges, int32_t* rounds) 
 
 cc_status cc_copy_nonloop(cc_ctx* c, int32_t* out, int64_t cap, int64_t* count) {
     CC_CHECK_CTX(c);
+    {
+        CC_DEVICE(c);
+        cc_status st = refresh_schedule_stats(c);
+        if (st != CC_OK) return st;
+    }
     if (count) *count = c->last_nonloop;
     const int64_t m = c->last_nonloop < cap ? c->last_nonloop : cap;
     if (m <= 0) return CC_OK;

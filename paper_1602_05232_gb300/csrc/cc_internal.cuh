@@ -119,6 +119,14 @@ cudaError_t launch_sv_round(const int* a2, const unsigned* m2, int* comp, unsign
 cudaError_t launch_join(const int* a2, const unsigned* m2, const int* comp, int* parent,
                         DevState* ds, int grid, int block, cudaStream_t s);
 
+// The hooking rounds as one executable CUDA graph: a while node repeats
+// {clear pc[1]; hook; jump; decide} on the device until a round hooks nothing.
+// pc: [0] |A''| (set by the relabel step), [1] hooked flag, [2] rounds run
+// (written by the graph). The graph holds these pointers and the launch shape;
+// rebuild it when any of them changes.
+cudaError_t build_sv_loop(const int* a2, unsigned* pc, int* comp, DevState* ds, int grid, int block,
+                          cudaGraphExec_t* out);
+
 // Union by size (the paper's schedule only) and the walks for forests that
 // do not keep parent[v] <= v.
 cudaError_t launch_relabel_generic(int* parent, int n, const int* edges, int64_t k, int* a2,

@@ -137,6 +137,86 @@ cudaError_t launch_join(const int* a2, const unsigned* m2, const int* comp, int*
     return cudaGetLastError();
 }
 
+// --- the hooking rounds as one CUDA graph with a device-side loop ----------
+//
+// pc[0] = |A''| (written by the relabel step), pc[1] = the hooked flag of the
+// round just run, pc[2] = rounds run so far. The graph is
+//   k_sv_start -> while (condition) { pc[1] = 0; k_sv_hook; k_sv_jump; k_sv_continue }
+// so the rounds repeat on the device until one hooks nothing, with no host
+// round trip between them.
+
+namespace {
+
+__global__ void k_sv_start(unsigned* __restrict__ pc, cudaGraphConditionalHandle h) {
+    pc[2] = 0u;
+    cudaGraphSetConditional(h, pc[0] > 0u ? 1u : 0u);  // an empty A'' needs no round
+}
+
+// Another round while the last one hooked. Each round that hooks removes at
+// least one component root, so more than 2|A''| + 1 rounds means a broken
+// forest: it is reported and the loop stops (the host loop's bound).
+__global__ void k_sv_continue(unsigned* __restrict__ pc, cudaGraphConditionalHandle h,
+                              DevState* __restrict__ ds) {
+    const unsigned r = ++pc[2];
+    unsigned go = pc[1] != 0u ? 1u : 0u;
+    if (go && r >= 2u * pc[0] + 1u) {
+        flag(ds, ST_CORRUPT);
+        go = 0u;
+    }
+    cudaGraphSetConditional(h, go);
+}
+
+}  // namespace
+
+cudaError_t build_sv_loop(const int* a2, unsigned* pc, int* comp, DevState* ds, int grid, int block,
+                          cudaGraphExec_t* out) {
+    *out = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    cudaGraphConditionalHandle h = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+    cudaGraphNode_t start = nullptr, loop = nullptr;
+    if (e == cudaSuccess) {
+        void* args[] = {&pc, &h};
+        cudaKernelNodeParams kp = {};
+        kp.func = reinterpret_cast<void*>(k_sv_start);
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(1);
+        kp.kernelParams = args;
+        e = cudaGraphAddKernelNode(&start, g, nullptr, 0, &kp);
+    }
+    cudaGraphNodeParams cp = {};
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&loop, g, &start, nullptr, 1, &cp);
+    }
+    // the loop body, recorded by capturing the round's launches into it
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = cudaMemsetAsync(pc + 1, 0, sizeof(unsigned), cs);
+        if (e1 == cudaSuccess) e1 = launch_sv_round(a2, pc, comp, pc + 1, grid, block, cs);
+        if (e1 == cudaSuccess) {
+            k_sv_continue<<<1, 1, 0, cs>>>(pc, h, ds);
+            e1 = cudaGetLastError();
+        }
+        cudaGraph_t body = nullptr;
+        e = cudaStreamEndCapture(cs, &body);
+        if (e == cudaSuccess) e = e1;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (cs) cudaStreamDestroy(cs);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) *out = nullptr;
+    return e;
+}
+
 }  // namespace cc
 
 // ---------------------------------------------------------------------------

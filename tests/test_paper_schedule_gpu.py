@@ -52,21 +52,24 @@ def run(cc, s, options, check_a2=True):
     f.sync()
 
 
-@pytest.mark.parametrize("opts", [{}, {"compress_every": 0}, {"compress_every": 3, "query_halving": 1}])
+@pytest.mark.parametrize("opts", [{}, {"compress_every": 0}, {"compress_every": 3, "query_halving": 1},
+                                  {"sv_graph": 0}, {"sv_graph": 0, "compress_every": 0}])
 def test_paper_schedule_uniform(cc, opts):
     run(cc, I.uniform_stream(), opts)
 
 
-def test_paper_schedule_rmat_and_grid(cc):
-    run(cc, I.rmat_stream(scale=16, m=1 << 19, batch=1 << 15, q=1 << 14, seed=3), {})
-    run(cc, I.grid_stream(256, 256, batch=4001, q=4096, seed=4), {"compress_every": 2})
+@pytest.mark.parametrize("sv_graph", [1, 0], ids=["rounds_as_graph", "rounds_from_host"])
+def test_paper_schedule_rmat_and_grid(cc, sv_graph):
+    run(cc, I.rmat_stream(scale=16, m=1 << 19, batch=1 << 15, q=1 << 14, seed=3), {"sv_graph": sv_graph})
+    run(cc, I.grid_stream(256, 256, batch=4001, q=4096, seed=4), {"compress_every": 2, "sv_graph": sv_graph})
 
 
-def test_paper_schedule_star_minibatch(cc):
+@pytest.mark.parametrize("sv_graph", [1, 0], ids=["rounds_as_graph", "rounds_from_host"])
+def test_paper_schedule_star_minibatch(cc, sv_graph):
     # the star of Section 3.2: on an empty graph A'' is the minibatch itself,
     # and one round of hooking joins v1..v8 under v1
     g = load_golden("star_minibatch.txt")
-    f = cc.Forest(g["n"], update_schedule=1)
+    f = cc.Forest(g["n"], update_schedule=1, sv_graph=sv_graph)
     f.bulk_update(dev(np.array(g["edges"], dtype=np.int32)))
     m, rounds = f.schedule_stats()
     assert m == 7 and rounds == 2           # one round hooks, the next finds nothing
@@ -79,9 +82,12 @@ def test_paper_schedule_hub_and_descending_path(cc):
     run(cc, I.hub_stream(n=1 << 16, m=1 << 18, batch=1 << 15, q=1 << 13, hub=0), {})
     n = 5000
     path = np.stack([np.arange(n - 1, 0, -1), np.arange(n - 2, -1, -1)], 1).astype(np.int32)
-    f = cc.Forest(n, update_schedule=1)
-    f.bulk_update(dev(path))
-    assert f.components() == 1 and int(f.labels().max()) == 0
+    for sv_graph in (1, 0):
+        f = cc.Forest(n, update_schedule=1, sv_graph=sv_graph)
+        f.bulk_update(dev(path))
+        assert f.components() == 1 and int(f.labels().max()) == 0
+        m, rounds = f.schedule_stats()
+        assert m == n - 1 and rounds >= 2
 
 
 def test_paper_schedule_full_size_rmat(cc):

@@ -229,6 +229,7 @@ OPTION_RANGES = [
     ("hook", [-1, 3], [0, 1, 2]),
     ("bulk_find", [2], [0, 1]),
     ("update_schedule", [2], [0, 1]),
+    ("sv_graph", [-1, 2], [0, 1]),
 ]
 
 
