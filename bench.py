@@ -700,6 +700,8 @@ def gather_ceiling(f, d_pairs, qoff, B: int, reps: int = 20) -> dict | None:
         return None
     f.compress()                                # flat forest: parent equality decides
     out = torch.empty(int(np.max(np.diff(qoff))), dtype=torch.uint8, device=d_pairs.device)
+    bulk_find = f.get_option("bulk_find")
+    f.set_option("bulk_find", 0)                # the plain query launch shape, whatever the options
     f.set_option("profile", 1)
     f.sync()
     f.kernel_stats(timing=True)                 # clears the timing sums
@@ -713,6 +715,7 @@ def gather_ceiling(f, d_pairs, qoff, B: int, reps: int = 20) -> dict | None:
     f.sync()
     launches, ms = f.kernel_stats(timing=True)["query"]
     f.set_option("profile", 0)
+    f.set_option("bulk_find", bulk_find)
     launches -= n0
     if launches <= 0 or ms <= 0:
         return None
