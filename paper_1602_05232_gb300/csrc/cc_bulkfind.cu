@@ -36,30 +36,47 @@ __device__ __forceinline__ unsigned rd_hash(int f, unsigned rho) {
     return (unsigned)(((unsigned long long)h * rho) >> 32);
 }
 
-// Append v to a list with one atomic per warp (every lane of the warp calls it).
-__device__ __forceinline__ void append1(bool has, int v, int* __restrict__ out,
-                                        unsigned* __restrict__ count) {
+// Append to a list with ONE atomic per block (rather than one per warp): every
+// frontier of a level grows through a single counter, and at a million
+// appends per launch the per-warp atomics on that one word queue up. The
+// warps' counts are scanned in shared memory by one thread, which takes the
+// block's range with one atomicAdd. Every thread of the block must call these
+// (they contain barriers). A warp reads and writes only its own count, the
+// write of the next call coming after that call's warp-wide ballot (which all
+// lanes reach only after their reads), and the scan and the base are rewritten
+// only after the next call's first barrier, so consecutive calls need no
+// barrier between them.
+__device__ __forceinline__ unsigned block_slot(bool has, unsigned* __restrict__ count) {
+    __shared__ unsigned warp_base[32];
+    __shared__ unsigned block_base;
     const unsigned mask = __ballot_sync(0xffffffffu, has);
-    if (!mask) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(mask) - 1;
-    unsigned base = 0;
-    if (lane == leader) base = atomicAdd(count, (unsigned)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (has) out[base + __popc(mask & ((1u << lane) - 1))] = v;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) warp_base[w] = __popc(mask);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned total = 0;
+        const int warps = (blockDim.x + 31) >> 5;
+        for (int j = 0; j < warps; j++) {
+            const unsigned c = warp_base[j];
+            warp_base[j] = total;
+            total += c;
+        }
+        block_base = total ? atomicAdd(count, total) : 0u;
+    }
+    __syncthreads();
+    return block_base + warp_base[w] + __popc(mask & ((1u << lane) - 1));
 }
 
-__device__ __forceinline__ void append2(bool has, int a, int b, int* __restrict__ out,
-                                        unsigned* __restrict__ count) {
-    const unsigned mask = __ballot_sync(0xffffffffu, has);
-    if (!mask) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(mask) - 1;
-    unsigned base = 0;
-    if (lane == leader) base = atomicAdd(count, (unsigned)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, leader);
+__device__ __forceinline__ void append1_block(bool has, int v, int* __restrict__ out,
+                                              unsigned* __restrict__ count) {
+    const unsigned slot = block_slot(has, count);
+    if (has) out[slot] = v;
+}
+
+__device__ __forceinline__ void append2_block(bool has, int a, int b, int* __restrict__ out,
+                                              unsigned* __restrict__ count) {
+    const unsigned slot = block_slot(has, count);
     if (has) {
-        const unsigned slot = base + __popc(mask & ((1u << lane) - 1));
         out[2 * slot] = a;
         out[2 * slot + 1] = b;
     }
@@ -77,7 +94,7 @@ k_bf_seed(const int* __restrict__ S, int64_t k, int n, int* __restrict__ mark, i
         if (in_range(s, n)) has = atomicExch(mark + s, epoch) != epoch;
         else flag(ds, ST_RANGE);
     }
-    append1(has, s, front, count);
+    append1_block(has, s, front, count);
 }
 
 // One Phase I level.
@@ -95,10 +112,10 @@ k_bf_up(const int* __restrict__ front, unsigned c, const int* __restrict__ paren
     }
     const bool is_root = live && p == v;
     const bool edge = live && p != v;
-    append1(is_root, v, roots, roots_count);
-    append2(edge, p, v, R, R_count);
+    append1_block(is_root, v, roots, roots_count);
+    append2_block(edge, p, v, R, R_count);
     const bool go_on = edge && atomicExch(mark + p, epoch) != epoch;
-    append1(go_on, p, next, next_count);
+    append1_block(go_on, p, next, next_count);
 }
 
 // atomicAdd(counter + key, 1) for every live lane, one atomic per distinct
@@ -190,7 +207,7 @@ k_bf_down_expand(const int* __restrict__ D, unsigned c, const int* __restrict__ 
             r = D[2 * lo + 1];
         }
     }
-    append2(has, u, r, next, next_count);
+    append2_block(has, u, r, next, next_count);
 }
 
 __global__ void __launch_bounds__(1024)
