@@ -75,7 +75,7 @@ def build_cc(force: bool = False) -> Path:
         obj = objdir / (cu.stem + ".o")
         objs.append(obj)
         cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, "-I", str(INCLUDE), "-I", str(CSRC),
-               "-dc" if False else "-c", str(cu), "-o", str(obj)]
+               "-c", str(cu), "-o", str(obj)]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE,
                                             stderr=subprocess.PIPE, text=True)))
     for cmd, p in procs:

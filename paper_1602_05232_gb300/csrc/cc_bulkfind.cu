@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "cc_append.cuh"
 #include "cc_device.cuh"
 #include "cc_internal.cuh"
 
@@ -34,52 +35,6 @@ namespace {
 __device__ __forceinline__ unsigned rd_hash(int f, unsigned rho) {
     const unsigned h = (unsigned)f * 0x9E3779B1u;
     return (unsigned)(((unsigned long long)h * rho) >> 32);
-}
-
-// Append to a list with ONE atomic per block (rather than one per warp): every
-// frontier of a level grows through a single counter, and at a million
-// appends per launch the per-warp atomics on that one word queue up. The
-// warps' counts are scanned in shared memory by one thread, which takes the
-// block's range with one atomicAdd. Every thread of the block must call these
-// (they contain barriers). A warp reads and writes only its own count, the
-// write of the next call coming after that call's warp-wide ballot (which all
-// lanes reach only after their reads), and the scan and the base are rewritten
-// only after the next call's first barrier, so consecutive calls need no
-// barrier between them.
-__device__ __forceinline__ unsigned block_slot(bool has, unsigned* __restrict__ count) {
-    __shared__ unsigned warp_base[32];
-    __shared__ unsigned block_base;
-    const unsigned mask = __ballot_sync(0xffffffffu, has);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) warp_base[w] = __popc(mask);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned total = 0;
-        const int warps = (blockDim.x + 31) >> 5;
-        for (int j = 0; j < warps; j++) {
-            const unsigned c = warp_base[j];
-            warp_base[j] = total;
-            total += c;
-        }
-        block_base = total ? atomicAdd(count, total) : 0u;
-    }
-    __syncthreads();
-    return block_base + warp_base[w] + __popc(mask & ((1u << lane) - 1));
-}
-
-__device__ __forceinline__ void append1_block(bool has, int v, int* __restrict__ out,
-                                              unsigned* __restrict__ count) {
-    const unsigned slot = block_slot(has, count);
-    if (has) out[slot] = v;
-}
-
-__device__ __forceinline__ void append2_block(bool has, int a, int b, int* __restrict__ out,
-                                              unsigned* __restrict__ count) {
-    const unsigned slot = block_slot(has, count);
-    if (has) {
-        out[2 * slot] = a;
-        out[2 * slot + 1] = b;
-    }
 }
 
 // F_0 = removeDup(S): the first lane to stamp a vertex with this epoch keeps it.

@@ -16,6 +16,7 @@
 // a smaller root), so the plain path's query and label kernels apply as is.
 #include <cstdint>
 
+#include "cc_append.cuh"
 #include "cc_device.cuh"
 #include "cc_internal.cuh"
 
@@ -23,24 +24,7 @@ namespace cc {
 
 namespace {
 
-// Append one pair per lane that has one, with one atomic per warp.
-__device__ __forceinline__ void append_pair(bool has, int a, int b, int* __restrict__ out,
-                                            unsigned* __restrict__ count) {
-    const unsigned mask = __ballot_sync(0xffffffffu, has);
-    if (!mask) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(mask) - 1;
-    unsigned base = 0;
-    if (lane == leader) base = atomicAdd(count, (unsigned)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (has) {
-        const unsigned slot = base + __popc(mask & ((1u << lane) - 1));
-        out[2 * slot] = a;
-        out[2 * slot + 1] = b;
-    }
-}
-
-// Step 1: one edge per thread. Every thread of a warp reaches the ballot.
+// Step 1: one edge per thread. Every thread of the block reaches the append.
 __global__ void __launch_bounds__(1024)
 k_relabel(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
           int* __restrict__ a2, unsigned* __restrict__ m2, int* __restrict__ comp,
@@ -63,7 +47,7 @@ k_relabel(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_
             flag(ds, ST_RANGE);
         }
     }
-    append_pair(has, ru, rv, a2, m2);
+    append2_block(has, ru, rv, a2, m2);
 }
 
 // Step 2a: hooking. The larger component root goes under the smaller one.
@@ -286,7 +270,7 @@ k_relabel_generic(int* __restrict__ parent, int n, const int* __restrict__ edges
             flag(ds, ST_RANGE);
         }
     }
-    append_pair(has, ru, rv, a2, m2);
+    append2_block(has, ru, rv, a2, m2);
 }
 
 // The vote key orders roots by size, then by smaller id.
@@ -472,7 +456,7 @@ k_filter_roots(const int* __restrict__ res, int64_t k, int* __restrict__ a2, uns
             }
         }
     }
-    append_pair(has, ru, rv, a2, m2);
+    append2_block(has, ru, rv, a2, m2);
 }
 }  // namespace
 
