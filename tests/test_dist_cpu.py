@@ -54,3 +54,24 @@ def test_two_gloo_ranks():
     assert [x[2] for x in res] == [3.0, 3.0]            # sum over ranks
     assert res[0][3] is False and res[0][4] == "reference"   # rank 0 runs the reference arm
     assert res[1][3] is True                             # rank 1 does no work
+
+
+def test_reference_arm_line_has_the_contract_keys():
+    """The --impl reference line (the oracle on the host) carries the keys the
+    bench contract asks for, with the GPU arm's metric and unit."""
+    sys.path.insert(0, str(ROOT))
+    import argparse
+    import bench
+    ns = argparse.Namespace(workload="uniform", steps=3, warmup=3, ref_fraction=64)
+    d = bench.run_reference(ns, 0, 1)
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "impl",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "edges/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 3
+    assert "workload" in d["config"]
+    cpu = d["cpu_baseline"]
+    assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and cpu["value"] == d["value"] and cpu["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
