@@ -67,7 +67,14 @@ def device_name() -> str:
 
 def tuned_options(workload: str, device: str | None = None) -> dict | None:
     """Cached best options for `workload` on `device` (default: the current
-    CUDA device), or None."""
+    CUDA device), or None.
+
+    The result may contain pdl=2 (programmatic dependent launch reading each
+    thread's first pairs before waiting for the previous kernel). That is only
+    valid when the edge/pair arrays are not written by the kernel launched just
+    before on the same stream -- true for the benchmarks' resident streams and
+    for inputs copied in, not for edges produced by a caller's own kernel
+    right before the call. Such callers set pdl to 1 (or 0)."""
     try:
         d = json.loads(CACHE.read_text())
         return dict(d[device or device_name()][workload]["options"])
