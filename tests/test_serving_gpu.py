@@ -52,9 +52,9 @@ def alone_answers(n, reqs, data):
     return want, uf.labels()
 
 
-def serve(cc, n, reqs, data, paced=False, batch=0, **cfg):
+def serve(cc, n, reqs, data, paced=False, batch=0, forest_opts=None, **cfg):
     """batch > 0: hand the requests over `batch` at a time (cc_server_enqueue_many)."""
-    f = cc.Forest(n)
+    f = cc.Forest(n, **(forest_opts or {}))
     outs = {}
     with cc.Server(f, **cfg) as srv:
         t0 = time.perf_counter()
@@ -84,17 +84,26 @@ def serve(cc, n, reqs, data, paced=False, batch=0, **cfg):
     return {i: o.numpy() for i, o in outs.items()}, labels, lat, st
 
 
-@pytest.mark.parametrize("mode", ["burst", "paced", "no_merge", "tiny_ring", "batched_enqueue"])
+@pytest.mark.parametrize("mode", ["burst", "paced", "no_merge", "tiny_ring", "batched_enqueue",
+                                  "early_pairs_tiny_ring"])
 def test_served_equals_alone(cc, mode):
     n, reqs, data = make_trace(scale=16, m=1 << 19, seed=7)
     want, want_labels = alone_answers(n, reqs, data)
     cfg = {}
     if mode == "no_merge":
         cfg = {"merge": False}
-    if mode == "tiny_ring":
+    forest_opts = None
+    if mode in ("tiny_ring", "early_pairs_tiny_ring"):
         cfg = {"ring_pairs": 1 << 12, "max_group_pairs": 1 << 11}
+    if mode == "early_pairs_tiny_ring":
+        # the kernels read their first pairs before waiting for the previous
+        # kernel (pdl 2); the ring is small, so its slots are reused constantly
+        # and a read that overtook its staging copy would see another
+        # request's pairs
+        forest_opts = {"pdl": 2, "update_variant": 3, "edges_per_thread": 2, "compress_every": 0}
     got, labels, lat, st = serve(cc, n, reqs, data, paced=(mode == "paced"),
-                                 batch=(97 if mode == "batched_enqueue" else 0), **cfg)
+                                 batch=(97 if mode == "batched_enqueue" else 0), forest_opts=forest_opts,
+                                 **cfg)
     for i, w in want.items():
         assert np.array_equal(got[i], w), f"request {i} differs from running it alone"
     assert np.array_equal(labels, want_labels)
