@@ -281,10 +281,32 @@ __device__ __forceinline__ unsigned long long vote_key(int size, int x) {
 __global__ void __launch_bounds__(1024)
 k_size_vote(const int* __restrict__ a2, const unsigned* __restrict__ m2, const int* __restrict__ comp,
             const int* __restrict__ size, unsigned long long* __restrict__ best) {
+    // Most endpoints of A'' vote in the same few components (small trees
+    // joining a giant one), so the votes are first reduced per component
+    // within the warp: one atomicMax per distinct component per warp instead
+    // of one per endpoint on the same word. The loop is warp-uniform so that
+    // every lane takes part in the warp-wide steps.
     const unsigned m2x2 = 2u * *m2;
-    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < m2x2; j += gridDim.x * blockDim.x) {
-        const int x = a2[j];
-        atomicMax(best + comp[x], vote_key(size[x], x));
+    const unsigned lane = threadIdx.x & 31u;
+    for (unsigned j0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); j0 < m2x2; j0 += gridDim.x * blockDim.x) {
+        const unsigned j = j0 + lane;
+        const bool live = j < m2x2;
+        int t = 0;
+        unsigned long long key = 0ull;
+        if (live) {
+            const int x = a2[j];
+            t = comp[x];
+            key = vote_key(size[x], x);
+        }
+        const unsigned active = __ballot_sync(0xffffffffu, live);
+        if (!live) continue;
+        const unsigned g = __match_any_sync(active, t);
+        unsigned long long m = key;
+        for (unsigned rest = g; rest; rest &= rest - 1) {
+            const unsigned long long o = __shfl_sync(g, key, __ffs(rest) - 1);
+            m = o > m ? o : m;
+        }
+        if ((unsigned)(__ffs(g) - 1) == lane) atomicMax(best + t, m);
     }
 }
 
@@ -292,15 +314,29 @@ __global__ void __launch_bounds__(1024)
 k_size_join(const int* __restrict__ a2, const unsigned* __restrict__ m2, const int* __restrict__ comp,
             const unsigned long long* __restrict__ best, int* __restrict__ parent,
             int* __restrict__ size, DevState* __restrict__ ds) {
+    // The sizes of the roots linked under one winner are summed within the
+    // warp first (one atomicAdd per winner per warp), for the same reason.
     const unsigned m2x2 = 2u * *m2;
+    const unsigned lane = threadIdx.x & 31u;
     int made = 0;
-    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < m2x2; j += gridDim.x * blockDim.x) {
-        const int x = a2[j];
-        const int w = (int)(0xffffffffu - (unsigned)(best[comp[x]] & 0xffffffffull));
-        if (w != x && atomicCAS(parent + x, x, w) == x) {
-            atomicAdd(size + w, size[x]);  // x is no longer a root: its size is final
-            made++;
+    for (unsigned j0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); j0 < m2x2; j0 += gridDim.x * blockDim.x) {
+        const unsigned j = j0 + lane;
+        bool linked = false;
+        int w = 0, sx = 0;
+        if (j < m2x2) {
+            const int x = a2[j];
+            w = (int)(0xffffffffu - (unsigned)(best[comp[x]] & 0xffffffffull));
+            if (w != x && atomicCAS(parent + x, x, w) == x) {
+                linked = true;
+                sx = size[x];  // x is no longer a root: its size is final
+                made++;
+            }
         }
+        const unsigned act = __ballot_sync(0xffffffffu, linked);
+        if (!linked) continue;
+        const unsigned g = __match_any_sync(act, w);
+        const int sum = __reduce_add_sync(g, sx);
+        if ((unsigned)(__ffs(g) - 1) == lane) atomicAdd(size + w, sum);
     }
     made = __reduce_add_sync(0xffffffffu, made);
     if ((threadIdx.x & 31) == 0 && made) atomicAdd(&ds->unions, (unsigned long long)made);
