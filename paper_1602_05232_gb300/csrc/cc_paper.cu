@@ -82,15 +82,30 @@ k_sv_jump(const int* __restrict__ a2, const unsigned* __restrict__ m2, int* __re
 
 // Step 3: join. Every root x of A'' is pointed at its component's smallest
 // root; the compare-and-swap lets exactly one of x's copies count the link.
+// A root that ends many A'' edges (a hub's) has many copies: within a warp
+// only one copy per distinct root tries, and a plain read that already shows
+// the root linked skips the compare-and-swap, so the copies do not queue on
+// its parent word. The loop is warp-uniform for the warp-wide steps.
 __global__ void __launch_bounds__(1024)
 k_join(const int* __restrict__ a2, const unsigned* __restrict__ m2, const int* __restrict__ comp,
        int* __restrict__ parent, DevState* __restrict__ ds) {
     const unsigned m2x2 = 2u * *m2;
+    const unsigned lane = threadIdx.x & 31u;
     int made = 0;
-    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < m2x2; j += gridDim.x * blockDim.x) {
-        const int x = a2[j];
-        const int r = comp[x];
-        if (r != x && atomicCAS(parent + x, x, r) == x) made++;
+    for (unsigned j0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); j0 < m2x2; j0 += gridDim.x * blockDim.x) {
+        const unsigned j = j0 + lane;
+        int x = -1, r = -1;
+        if (j < m2x2) {
+            x = a2[j];
+            r = comp[x];
+        }
+        const bool live = j < m2x2 && r != x;
+        const unsigned act = __ballot_sync(0xffffffffu, live);
+        if (!live) continue;
+        const unsigned g = __match_any_sync(act, x);
+        if ((unsigned)(__ffs(g) - 1) == lane && *(volatile const int*)(parent + x) == x &&
+            atomicCAS(parent + x, x, r) == x)
+            made++;
     }
     made = __reduce_add_sync(0xffffffffu, made);
     if ((threadIdx.x & 31) == 0 && made) atomicAdd(&ds->unions, (unsigned long long)made);
