@@ -69,7 +69,17 @@ k_bf_up(const int* __restrict__ front, unsigned c, const int* __restrict__ paren
     const bool edge = live && p != v;
     append1_block(is_root, v, roots, roots_count);
     append2_block(edge, p, v, R, R_count);
-    const bool go_on = edge && atomicExch(mark + p, epoch) != epoch;
+    // Only the first to stamp p carries the flow on. Many frontier nodes share
+    // a parent (a big tree's root): within a warp one lane per distinct parent
+    // stamps it, and a read that already shows this call's stamp skips the
+    // exchange, so the nodes do not queue on that one mark word.
+    const unsigned act = __ballot_sync(0xffffffffu, edge);
+    bool go_on = false;
+    if (edge) {
+        const unsigned g = __match_any_sync(act, p);
+        if ((unsigned)(__ffs(g) - 1) == (threadIdx.x & 31u))
+            go_on = *(volatile const int*)(mark + p) != epoch && atomicExch(mark + p, epoch) != epoch;
+    }
     append1_block(go_on, p, next, next_count);
 }
 
