@@ -42,12 +42,20 @@ __global__ void __launch_bounds__(1024)
 k_bf_seed(const int* __restrict__ S, int64_t k, int n, int* __restrict__ mark, int epoch,
           int* __restrict__ front, unsigned* __restrict__ count, DevState* __restrict__ ds) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool has = false;
+    bool has = false, ok = false;
     int s = 0;
     if (i < k) {
         s = S[i];
-        if (in_range(s, n)) has = atomicExch(mark + s, epoch) != epoch;
-        else flag(ds, ST_RANGE);
+        ok = in_range(s, n);
+        if (!ok) flag(ds, ST_RANGE);
+    }
+    // Query sets repeat popular vertices: one lane per distinct vertex per
+    // warp stamps it, after a read that does not already show this call's stamp.
+    const unsigned act = __ballot_sync(0xffffffffu, ok);
+    if (ok) {
+        const unsigned g = __match_any_sync(act, s);
+        if ((unsigned)(__ffs(g) - 1) == (threadIdx.x & 31u))
+            has = *(volatile const int*)(mark + s) != epoch && atomicExch(mark + s, epoch) != epoch;
     }
     append1_block(has, s, front, count);
 }
