@@ -372,7 +372,10 @@ cudaError_t bulk_find(BulkFindState& b, int* parent, int n, const int* S, int64_
             if (R_total)
                 e = cudaMemcpyAsync(q, b.R, sizeof(int) * 2 * (size_t)R_total, cudaMemcpyDeviceToDevice, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) return e;
+            if (e != cudaSuccess) {
+                cudaFree(q);
+                return e;
+            }
             cudaFree(b.R);
             b.R = q;
             b.cap_R = cap;
