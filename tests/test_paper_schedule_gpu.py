@@ -102,3 +102,30 @@ def test_paper_schedule_full_size_rmat(cc):
         ref.bulk_update(e)
         assert np.array_equal(f.bulk_query(dev(q)).cpu().numpy(), ref.bulk_query(q)), i
     assert np.array_equal(f.labels().cpu().numpy(), ref.labels())
+
+
+def test_paper_schedule_unaligned_ragged_and_out_of_range(cc):
+    # edge arrays 8 and 4 bytes past a 16-byte boundary, odd lengths (a ragged
+    # last thread), and ids outside [0, n) that are skipped and reported
+    s = I.uniform_stream(n=5000, m=3 * 12001, batch=12001, q=7001, seed=9)
+    for shift in (2, 1):
+        f = cc.Forest(s.n, update_schedule=1)
+        ref = oracle.OracleUF(s.n)
+        for i, (e, q) in enumerate(s):
+            e = e.copy()
+            e[::997, i % 2] = -1 - i          # negative ids
+            e[5::1009, 1 - i % 2] = s.n + i   # ids >= n
+            want_a2 = ref.relabel(e)
+            buf = torch.zeros(e.size + 4, dtype=torch.int32, device="cuda")
+            buf[shift:shift + e.size] = dev(e.ravel())
+            f.bulk_update(buf[shift:shift + e.size])
+            ref.bulk_update(e)
+            m, _ = f.schedule_stats()
+            assert m == len(want_a2), (shift, i)
+            assert np.array_equal(sorted_pairs(f.nonloop_edges().cpu().numpy()), sorted_pairs(want_a2))
+            with pytest.raises(cc.CCError) as ex:
+                f.sync()
+            assert ex.value.status == cc.CC_ERR_RANGE
+            assert np.array_equal(f.bulk_query(dev(q)).cpu().numpy(), ref.bulk_query(q)), (shift, i)
+        assert np.array_equal(f.labels().cpu().numpy(), ref.labels())
+        f.sync()
