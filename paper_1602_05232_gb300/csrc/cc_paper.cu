@@ -36,8 +36,11 @@ k_relabel(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_
         int u[1], v[1];
         load_pairs<1>(edges, i, k, vec, u, v);
         if (in_range(u[0], n) && in_range(v[0], n)) {
-            ru = find_halving(parent, u[0], ds);
-            rv = find_halving(parent, v[0], ds);
+            // both first parent reads in flight together; a parent read before
+            // the other walk's halving writes is still an ancestor of v
+            const int pu = parent[u[0]], pv = parent[v[0]];
+            ru = pu == u[0] ? u[0] : find_from(parent, u[0], pu, ds);
+            rv = pv == v[0] ? v[0] : find_from(parent, v[0], pv, ds);
             if (ru != rv) {
                 has = true;
                 comp[ru] = ru;  // every endpoint of A'' starts as its own component
