@@ -303,6 +303,14 @@ def pin_relabel(lib) -> list[str]:
         fails.append("star: repeating the minibatch leaves only self-loops")
     if uf.relabel(np.array([[0, 8]], dtype=np.int32)).tolist() != [[0, 1]]:
         fails.append("star: an edge into the star relabels to the star's smallest id")
+    # the range rule: an edge with an id outside [0, n) is dropped from A''
+    # (as Bulk-Update skips it); ids 0 and n - 1 are in range
+    n = 10
+    uf = _uf(lib, n)
+    uf.bulk_update(np.array([[1, 2]], dtype=np.int32))
+    e = np.array([[0, 9], [-1, 3], [2, 3], [4, n], [2**31 - 1, 0], [9, 1]], dtype=np.int32)
+    if uf.relabel(e).tolist() != [[0, 9], [1, 3], [9, 1]]:
+        fails.append("relabel: out-of-range edges dropped, boundary ids kept")
     return fails
 
 
