@@ -1,21 +1,28 @@
 """Benchmark: bulk incremental connectivity on one GB300 (or N replicas).
 
-Workload (default ``rmat``): one forest on n = 2^24 vertices fed by 2^27
-R-MAT edges (a, b, c, d = 0.57, 0.19, 0.19, 0.05, ids randomly permuted,
-seed = rank) in 128 minibatches of 2^20 edges; after each Bulk-Update, one
-Bulk-Query of 2^20 uniform vertex pairs. A STEP is one minibatch of that
-stream: the Bulk-Update, its compression pass and the Bulk-Query. Step i
-processes minibatch i mod 128; at each wrap the forest is reset to n
-singletons inside the step, so every pass starts from the empty graph.
+Headline workload (default ``grid``): one forest on the 8192 x 8192
+4-neighbour grid (n = 2^26, a 256 MiB forest, larger than L2), fed its
+134,201,344 edges, shuffled, in 32 minibatches of 2^22; after each
+Bulk-Update, one Bulk-Query of 2^22 uniform vertex pairs. A STEP is one whole
+pass of that stream from the empty graph: a reset of the forest to n
+singletons, then every minibatch's Bulk-Update (with the compression policy)
+and Bulk-Query in order. Throughput is total edges over total time (Section
+5.3, Table 3).
 
-Timing: W warm-up steps on a separate pass, reset, then exactly K steps
-bracketed by a barrier and a device synchronise, timed with CUDA events on
-the forest's stream; the max over ranks is reported. The 1 GiB edge stream
-and 1 GiB pair stream are larger than L2 and each is read once per pass (the
-64 MiB forest stays resident, as it does between minibatches in use).
+Timing: W untimed passes, then exactly K passes bracketed by a barrier and a
+device synchronise, timed with CUDA events on the forest's stream; the max
+over ranks is reported. The edge and pair streams (1 GiB each) are larger
+than L2 and each is read once per pass.
+
+The same JSON line carries the other forms (``--forms``): the plain form on
+the R-MAT n=2^24 and uniform n=2^16 streams (same step definition), the
+batched form (1024 segmented graphs, one persistent kernel replayed as a CUDA
+graph) against one launch per minibatch, and the served form (continuous
+batching over an R-MAT n=2^26, 2^30-edge request trace) against one request
+at a time.
 
 ``--impl reference`` times the CPU oracle (sequential union-find with path
-compression) on a bounded sample of each step's minibatch.
+compression) on a bounded sample of every pass.
 """
 from __future__ import annotations
 
@@ -340,39 +347,110 @@ def run_segmented(args, rank: int, world: int, local_rank: int, dist) -> dict:
 
 # ------------------------------------------------------------ serving form
 
+class ServingTrace:
+    """The served workload: one R-MAT stream of 2^(scale+4) edges (scale 26:
+    n = 2^26, 2^30 edges) in pinned host memory, and the request trace over
+    it (Poisson arrivals; updates of log-uniform [2^8, 2^20] edges taken from
+    the stream in order, queries of log-uniform [2^8, 2^18] uniform pairs, at
+    3:1). `views` holds each request's host tensors; `many` the same requests
+    as the arrays cc_server_enqueue_many takes."""
+
+    NOMINAL_HZ = 1000.0
+
+    def __init__(self, scale: int = 26, seed: int = 0):
+        import torch
+        from paper_1602_05232_gb300 import inputs as I
+        self.scale = scale
+        self.m = 1 << (scale + 4)
+        self.stream = I.rmat_stream(scale=scale, m=self.m, batch=self.m, q=1, seed=seed)
+        self.n = self.stream.n
+        self.h_edges = torch.empty((self.m, 2), dtype=torch.int32, pin_memory=True)
+        self.stream.all_edges(out=self.h_edges.numpy())
+        self.reqs = I.request_trace(self.m, rate_hz=self.NOMINAL_HZ, seed=seed)
+        self.qtot = sum(r.size for r in self.reqs if r.kind == 1)
+        self.h_pairs = torch.empty((self.qtot, 2), dtype=torch.int32, pin_memory=True)
+        I.uniform_pairs(self.n, self.qtot, seed, I.TAG_QUERIES, 0, out=self.h_pairs.numpy())
+        self.h_out = torch.zeros(self.qtot, dtype=torch.uint8, pin_memory=True)
+        self.views = []
+        for r in self.reqs:
+            if r.kind == 0:
+                self.views.append((0, self.h_edges[r.offset:r.offset + r.size], None))
+            else:
+                self.views.append((1, self.h_pairs[r.offset:r.offset + r.size],
+                                   self.h_out[r.offset:r.offset + r.size]))
+        self.many = (np.array([kind for kind, _, _ in self.views], dtype=np.int32),
+                     np.array([d.data_ptr() for _, d, _ in self.views], dtype=np.uint64),
+                     np.array([d.shape[0] for _, d, _ in self.views], dtype=np.int64),
+                     np.array([o.data_ptr() if o is not None else 0 for _, _, o in self.views],
+                              dtype=np.uint64))
+
+
+def host_memory_state(tensors=()) -> dict:
+    """Host-side evidence for run-to-run changes of the served form: kernel
+    memory-compaction and huge-page counters (/proc/vmstat), free and huge
+    memory (/proc/meminfo), and how the pinned buffers in `tensors` are
+    mapped (page size, huge pages) according to /proc/self/smaps."""
+    out = {}
+    want_vm = ("compact_stall", "compact_fail", "compact_success", "thp_fault_alloc",
+               "thp_fault_fallback", "pgmajfault", "numa_hint_faults", "pgmigrate_success")
+    try:
+        for line in open("/proc/vmstat"):
+            k, v = line.split()
+            if k in want_vm:
+                out[k] = int(v)
+    except OSError:
+        pass
+    want_mi = ("MemFree", "MemAvailable", "AnonHugePages", "HugePages_Total", "HugePages_Free",
+               "Hugepagesize", "Mlocked")
+    try:
+        for line in open("/proc/meminfo"):
+            k, _, v = line.partition(":")
+            if k in want_mi:
+                out[k] = v.strip()
+    except OSError:
+        pass
+    if tensors:
+        spans = [(t.data_ptr(), t.data_ptr() + t.numel() * t.element_size()) for t in tensors]
+        maps = []
+        try:
+            cur = None
+            for line in open("/proc/self/smaps"):
+                head = line.split()
+                if "-" in head[0] and len(head) >= 5 and ":" not in head[0]:
+                    lo, hi = (int(x, 16) for x in head[0].split("-"))
+                    cur = {"lo": lo, "hi": hi} if any(a < hi and lo < b for a, b in spans) else None
+                    if cur is not None:
+                        maps.append(cur)
+                elif cur is not None and head[0] in ("KernelPageSize:", "AnonHugePages:", "Rss:",
+                                                     "Locked:"):
+                    cur[head[0][:-1]] = " ".join(head[1:])
+        except OSError:
+            pass
+        out["pinned_mappings"] = len(maps)
+        out["pinned_GiB"] = round(sum(m["hi"] - m["lo"] for m in maps) / 2**30, 2)
+        out["pinned_page_sizes"] = sorted({m.get("KernelPageSize", "?") for m in maps})
+        out["pinned_anon_huge_kB"] = sum(int(m.get("AnonHugePages", "0 kB").split()[0]) for m in maps)
+    return out
+
+
 def run_serving(args, rank: int, world: int, local_rank: int, dist) -> dict:
     """Served form: the whole request trace through cc_server (continuous
     batching). Saturation: every request enqueued at once, edges/s from first
     enqueue to drain. Then the trace replayed at 0.5 / 0.8 / 0.95 of that
-    capacity with Poisson arrivals for p50/p99 latency. Plain form: the same
-    requests one at a time (copy in, one launch, copy out, wait)."""
+    capacity with Poisson arrivals for p50/p99 latency from arrival to
+    completion. Plain form: the same requests one at a time (copy in, one
+    launch, copy out, wait)."""
     import torch
-    from paper_1602_05232_gb300 import cc, inputs as I
+    from paper_1602_05232_gb300 import cc
 
     torch.cuda.set_device(local_rank)
     scale = args.serve_scale
-    m = 1 << (scale + 4)
-    s = I.rmat_stream(scale=scale, m=m, batch=m, q=1, seed=rank)
-    h_edges = torch.empty((m, 2), dtype=torch.int32, pin_memory=True)
-    s.all_edges(out=h_edges.numpy())
-    nominal = 1000.0
-    reqs = I.request_trace(m, rate_hz=nominal, seed=rank)
-    qtot = sum(r.size for r in reqs if r.kind == 1)
-    h_pairs = torch.empty((qtot, 2), dtype=torch.int32, pin_memory=True)
-    I.uniform_pairs(s.n, qtot, rank, I.TAG_QUERIES, 0, out=h_pairs.numpy())
-    h_out = torch.empty(qtot, dtype=torch.uint8, pin_memory=True)
-    views = []
-    for r in reqs:
-        if r.kind == 0:
-            views.append((0, h_edges[r.offset:r.offset + r.size], None))
-        else:
-            views.append((1, h_pairs[r.offset:r.offset + r.size], h_out[r.offset:r.offset + r.size]))
+    tr = ServingTrace(scale, seed=rank)
+    s, m, reqs, views, many = tr.stream, tr.m, tr.reqs, tr.views, tr.many
+    qtot = tr.qtot
+    nominal = tr.NOMINAL_HZ
     opts = launch_options("serving")
-    # the same requests as arrays, for handing them all over in one call
-    many = (np.array([kind for kind, _, _ in views], dtype=np.int32),
-            np.array([d.data_ptr() for _, d, _ in views], dtype=np.uint64),
-            np.array([d.shape[0] for _, d, _ in views], dtype=np.int64),
-            np.array([o.data_ptr() if o is not None else 0 for _, _, o in views], dtype=np.uint64))
+    mem_before = host_memory_state((tr.h_edges, tr.h_pairs, tr.h_out))
 
     def serve(rate: float | None, at_once: bool = False):
         f = cc.Forest(s.n, **opts)
@@ -400,11 +478,14 @@ def run_serving(args, rank: int, world: int, local_rank: int, dist) -> dict:
     serve(None)                                  # warm-up
     dist_barrier(dist)
     with ClockSampler(local_rank) as clk:
-        # saturation: every request is there at the start, handed over in one call
-        dt_sat, lat_sat, st_sat, lab_served = serve(None, at_once=True)
+        # saturation: every request is there at the start, handed over in one
+        # call; three runs in a row, to show whether the rate holds
+        sat_runs = [serve(None, at_once=True) for _ in range(3)]
+        dt_sat, lat_sat, st_sat, lab_served = sorted(sat_runs, key=lambda r: r[0])[1]   # the median run
         # the same with one enqueue call per request (the caller's loop is in the time)
         dt_sat1, _, st_sat1, _ = serve(None)
     dist_barrier(dist)
+    mem_after = host_memory_state((tr.h_edges, tr.h_pairs, tr.h_out))
     cap_edges = m / dt_sat
     cap_rps = len(reqs) / dt_sat
     loads = {}
@@ -445,6 +526,9 @@ def run_serving(args, rank: int, world: int, local_rank: int, dist) -> dict:
                    f"serving trace on R-MAT scale {scale}", "n": s.n, "edges": m,
                    "requests": len(reqs), "query_pairs": qtot, "options": opts},
         "saturation": {"edges_per_s": round(cap_edges, 1), "req_per_s": round(cap_rps, 1),
+                       "runs_edges_per_s": [round(m / r[0], 1) for r in sat_runs],
+                       "runs_what": "three saturation runs in a row in this process (new forest and "
+                                    "server each); the value is the median run",
                        "p50_ms": round(1e3 * float(np.percentile(lat_sat, 50)), 3),
                        "p99_ms": round(1e3 * float(np.percentile(lat_sat, 99)), 3),
                        "groups": st_sat["groups"],
@@ -456,6 +540,7 @@ def run_serving(args, rank: int, world: int, local_rank: int, dist) -> dict:
         "plain_form": {"edges_per_s": round(m / dt_plain, 1), "seconds": round(dt_plain, 3),
                        "what": "each request alone: copy in, one launch, copy out, synchronise"},
         "served_labels_equal_plain": same,
+        "host_memory": {"before": mem_before, "after": mem_after},
         "clocks": clk.summary(),
     }
 
@@ -537,13 +622,23 @@ def run_paper(args, rank: int, world: int, local_rank: int, dist) -> dict:
 
 # --------------------------------------------------------------- GPU arm
 
-def run_gpu(args, rank: int, world: int, local_rank: int, dist) -> dict | None:
+def run_gpu(args, rank: int, world: int, local_rank: int, dist, workload: str | None = None,
+            steps: int | None = None, warmup: int | None = None, e2e: bool = True,
+            cpu: bool = True) -> dict | None:
+    """Plain form on one minibatch stream. A STEP is one whole pass of the
+    stream from the empty graph: a reset of the forest to n singletons, then
+    every minibatch's Bulk-Update (with the compression policy) and
+    Bulk-Query in stream order. Throughput is total edges over total time, as
+    in Section 5.3; latency is per minibatch (update + query) and per pass."""
     import torch
     from paper_1602_05232_gb300 import cc
 
+    workload = workload or args.workload
+    K = args.steps if steps is None else steps
+    W = args.warmup if warmup is None else warmup
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    s = make_stream(args.workload, seed=rank)
+    s = make_stream(workload, seed=rank)
     B = s.batches
     # whole stream in pinned host memory, then resident in HBM
     h_edges = torch.empty((s.m, 2), dtype=torch.int32, pin_memory=True)
@@ -555,72 +650,84 @@ def run_gpu(args, rank: int, world: int, local_rank: int, dist) -> dict | None:
     d_pairs = h_pairs.to(dev)
     d_out = torch.empty(s.q, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
-    opts = launch_options(args.workload)
+    opts = launch_options(workload)
+    # every minibatch's views, made once (no slicing inside the timed regions)
+    views = [(d_edges[eoff[b]:eoff[b + 1]], d_pairs[qoff[b]:qoff[b + 1]], d_out[qoff[b]:qoff[b + 1]])
+             for b in range(B)]
 
     with torch.cuda.stream(stream):
         f = cc.Forest(s.n, stream=stream, **opts)
 
-    def step(i: int, ev: list | None = None) -> None:
-        b = i % B
-        if b == 0 and i > 0:
-            f.reset()
-        e = d_edges[eoff[b]:eoff[b + 1]]
-        q = d_pairs[qoff[b]:qoff[b + 1]]
-        f.bulk_update(e)
-        f.bulk_query(q, out=d_out[qoff[b]:qoff[b + 1]])
-
-    # warm-up pass, then back to the empty graph
-    for i in range(args.warmup):
-        step(i)
-    edges_per_step = [int(eoff[(i % B) + 1] - eoff[i % B]) for i in range(args.steps)]
-    pairs_per_step = [int(qoff[(i % B) + 1] - qoff[i % B]) for i in range(args.steps)]
-
-    def region(per_step_events: bool, profile: bool):
-        """K steps from the empty graph, timed on the forest's stream."""
+    def one_pass(ev: list | None = None) -> None:
         f.reset()
+        for b, (e, q, o) in enumerate(views):
+            f.bulk_update(e)
+            f.bulk_query(q, out=o)
+            if ev is not None:
+                ev[b].record(stream)
+
+    for _ in range(W):
+        one_pass()
+    stream.synchronize()
+
+    def region(batch_events: bool, profile: bool):
+        """K passes, timed on the forest's stream."""
         f.set_option("profile", 1 if profile else 0)
         stream.synchronize()
         f.kernel_stats(timing=profile)    # clears the timing sums
         l0 = f.kernel_stats()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1 if per_step_events else 2)]
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        bev = [[torch.cuda.Event(enable_timing=True) for _ in range(B)] for _ in range(K)] \
+            if batch_events else None
+        pev = [torch.cuda.Event(enable_timing=True) for _ in range(K)] if batch_events else None
         dist_barrier(dist)
         torch.cuda.synchronize(dev)
-        ev[0].record(stream)
-        for i in range(args.steps):
-            step(i)
-            if per_step_events:
-                ev[i + 1].record(stream)
-        ev[-1].record(stream)
+        start.record(stream)
+        for i in range(K):
+            one_pass(bev[i] if bev else None)
+            if pev:
+                pev[i].record(stream)
+        stop.record(stream)
         torch.cuda.synchronize(dev)
         dist_barrier(dist)
         ks = f.kernel_stats(timing=profile) if profile else None
         l1 = f.kernel_stats()
         f.set_option("profile", 0)
-        step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)] if per_step_events else None
-        return ev[0].elapsed_time(ev[-1]), step_ms, ks, l0, l1
+        batch_ms = pass_ms = None
+        if batch_events:
+            batch_ms, pass_ms, prev = [], [], start
+            for i in range(K):
+                # a pass's first minibatch also carries that pass's reset
+                for b in range(B):
+                    batch_ms.append(prev.elapsed_time(bev[i][b]))
+                    prev = bev[i][b]
+                pass_ms.append((start if i == 0 else pev[i - 1]).elapsed_time(pev[i]))
+                prev = pev[i]
+        return start.elapsed_time(stop), batch_ms, pass_ms, ks, l0, l1
 
-    # (A) the value: nothing but the K steps between two events
+    # (A) the value: nothing but the K passes between two events
     with ClockSampler(local_rank) as clk:
-        total_ms, _, _, la0, la1 = region(False, False)
-        # (B) per-step events for the latency distribution
-        _, step_ms, _, _, _ = region(True, False)
-        # (C) per-kernel events for the roofline
-        _, _, kstats, launches0, launches1 = region(False, True)
+        total_ms, _, _, _, la0, la1 = region(False, False)
+        # (B) an event after every minibatch, for the latency distributions
+        _, batch_ms, pass_ms, _, _, _ = region(True, False)
+        # (C) libcc's per-kernel events, for the roofline
+        _, _, _, kstats, launches0, launches1 = region(False, True)
     gpu_launches = sum(la1[k] - la0[k] for k in la1)
     depth_max, depth_mean = f.depth()
     f.sync()
-    gather = gather_ceiling(f, d_pairs, qoff, B)
+    gather = gather_ceiling(f, views)
 
     total_ms_max = dist_max(dist, total_ms, dev)
-    edges_all = dist_sum(dist, float(sum(edges_per_step)), dev)
-    pairs_all = dist_sum(dist, float(sum(pairs_per_step)), dev)
+    edges_all = dist_sum(dist, float(K * s.m), dev)
+    pairs_all = dist_sum(dist, float(K * s.q), dev)
     value = edges_all / (total_ms_max / 1e3)
 
     # per-kernel breakdown and the roofline of the dominant kernel
     peak, peak_kind = hbm_peak()
-    units = {"update": sum(edges_per_step), "query": sum(pairs_per_step),
+    units = {"update": K * s.m, "query": K * s.q,
              "compress_all": s.n * (launches1["compress_all"] - launches0["compress_all"]),
-             "compress_touched": sum(edges_per_step),
+             "compress_touched": K * s.m,
              "reset": s.n * (launches1["reset"] - launches0["reset"])}
     kernels = {}
     for k, (_, ms) in kstats.items():
@@ -641,7 +748,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int, dist) -> dict | None:
                 "peak_source": f"of {peak_kind}",
                 "bytes_per_unit": BYTES_PER_UNIT[dom],
                 "units_per_launch": per_launch_units,
-                "traffic": ncu_traffic(dom, args.workload)}
+                "traffic": ncu_traffic(dom, workload),
+                "timing_basis": "per-kernel events, PDL serialised",
+                "in_step_share": round(dk["ms_total"] / total_ms, 4),
+                "in_step_share_what": "the dominant kernel's summed event time over the same K "
+                                      "passes / the pass time of the value's region"}
     if gather:
         gather["frac_of_peak"] = round(gather["GBps"] / peak, 4)
         gather["dominant_kernel_frac_of_this"] = round(achieved / gather["GBps"], 4)
@@ -649,57 +760,62 @@ def run_gpu(args, rank: int, world: int, local_rank: int, dist) -> dict | None:
 
     upd_ms = sum(kstats[k][1] for k in ("update", "compress_all", "compress_touched"))
     qry_ms = kstats["query"][1]
-    e2e = run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist) if not args.no_e2e else None
+    e2e_out = run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist, workload, K, W) if e2e else None
 
     f.close()
-    del d_edges, d_pairs
+    del views, d_edges, d_pairs, d_out
     torch.cuda.empty_cache()
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(s, h_edges.numpy(), h_pairs.numpy(), eoff, qoff, args.cpu_seconds)
+    cpu_out = None
+    if cpu and rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_out = cpu_baseline(s, h_edges.numpy(), h_pairs.numpy(), eoff, qoff, args.cpu_seconds)
 
-    lat = sorted(step_ms)
+    def pct(xs, q):
+        xs = sorted(xs)
+        return round(xs[min(len(xs) - 1, int(q * len(xs)))], 4)
+
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "edges/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms_max / args.steps, 5),
+        "steps": K, "warmup": W, "ms_per_step": round(total_ms_max / K, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded R-MAT / uniform / grid generators; no dataset)",
-        "config": {"workload": WORKLOAD_TEXT.get(args.workload, s.name), "n": s.n, "edges_per_pass": s.m,
+        "config": {"workload": WORKLOAD_TEXT.get(workload, s.name), "n": s.n, "edges_per_pass": s.m,
+                   "queries_per_pass": s.q, "minibatches_per_pass": B,
                    "batch": int(eoff[1]), "query_batch": int(qoff[1]),
+                   "step": "one whole pass of the stream from the empty graph (reset, then every "
+                           "minibatch's Bulk-Update and Bulk-Query in order)",
                    "form": "plain (one launch per bulk operation)", "options": opts,
-                   "l2": "inputs larger than L2: 1 GiB edge + 1 GiB pair streams, each read "
-                         "once per pass; the forest (4n bytes) persists across steps",
+                   "l2": f"inputs larger than L2: {8 * s.m / 2**30:.2f} GiB of edges and "
+                         f"{8 * s.q / 2**30:.2f} GiB of pairs, each read once per pass",
                    "parallelism": f"replicas x{world} (independent streams, no collective)"},
         "queries_per_s": round(pairs_all / (total_ms_max / 1e3), 1),
-        "update_edges_per_s_kernels": round(sum(edges_per_step) / (upd_ms / 1e3), 1) if upd_ms else None,
-        "query_per_s_kernel": round(sum(pairs_per_step) / (qry_ms / 1e3), 1) if qry_ms else None,
-        "latency_ms": {"p50": round(lat[len(lat) // 2], 4),
-                       "p99": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 4),
-                       "what": "device time of one step (update + compress + query), from a "
-                               "second pass of the K steps with an event after each step"},
-        "timing": "value from K steps between two events with nothing else recorded; latency "
-                  "and the per-kernel times (roofline) from two more passes over the same K steps",
+        "update_edges_per_s_kernels": round(K * s.m / (upd_ms / 1e3), 1) if upd_ms else None,
+        "query_per_s_kernel": round(K * s.q / (qry_ms / 1e3), 1) if qry_ms else None,
+        "latency_ms": {"batch_p50": pct(batch_ms, 0.5), "batch_p99": pct(batch_ms, 0.99),
+                       "pass_p50": pct(pass_ms, 0.5), "pass_p99": pct(pass_ms, 0.99),
+                       "what": "device time of one minibatch (Bulk-Update + its compression + "
+                               "Bulk-Query; the first of a pass also its reset) and of one pass, "
+                               "from a second run of the K passes with an event after each minibatch"},
+        "timing": "value from K passes between two events with nothing else recorded; latency "
+                  "and the per-kernel times (roofline) from two more runs of the same K passes",
         "forest_depth": {"max": depth_max, "mean": round(depth_mean, 4),
-                         "what": "distance from a vertex to its root after the timed steps"},
+                         "what": "distance from a vertex to its root after the timed passes"},
         "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
-        "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu,
+        "clocks": clk.summary(), "e2e": e2e_out, "cpu_baseline": cpu_out,
     }
     return out
 
 
-def gather_ceiling(f, d_pairs, qoff, B: int, reps: int = 20) -> dict | None:
+def gather_ceiling(f, views, reps: int = 20) -> dict | None:
     """Context for the roofline: the query launch shape doing nothing but its
     gathers. After a full compression every vertex points at its root, so a
     query is decided by parent[u] == parent[v]: one streamed pair and two
     random 4-byte reads, the minimum any update or query of this layout pays.
     Timed with libcc's per-kernel events, like the kernels of the timed
     regions, and run after them (it changes the forest)."""
-    import torch
     if f.kernel_stats().get("query") is None:
         return None
     f.compress()                                # flat forest: parent equality decides
-    out = torch.empty(int(np.max(np.diff(qoff))), dtype=torch.uint8, device=d_pairs.device)
     bulk_find = f.get_option("bulk_find")
     f.set_option("bulk_find", 0)                # the plain query launch shape, whatever the options
     f.set_option("profile", 1)
@@ -708,9 +824,8 @@ def gather_ceiling(f, d_pairs, qoff, B: int, reps: int = 20) -> dict | None:
     n0 = f.kernel_stats()["query"]
     pairs = 0
     for r in range(reps):
-        b = r % B
-        q = d_pairs[qoff[b]:qoff[b + 1]]
-        f.bulk_query(q, out=out[:q.shape[0]])
+        _, q, o = views[r % len(views)]
+        f.bulk_query(q, out=o)
         pairs += q.shape[0]
     f.sync()
     launches, ms = f.kernel_stats(timing=True)["query"]
@@ -727,9 +842,11 @@ def gather_ceiling(f, d_pairs, qoff, B: int, reps: int = 20) -> dict | None:
                     "practical ceiling of this access pattern on this GPU, beside the copy-bandwidth peak"}
 
 
-def run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist) -> dict:
+def run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist, workload: str, K: int, W: int) -> dict:
     """Same metric through the public API from HOST buffers (pinned), with the
-    host<->device traffic of every step inside the timed region, two ways:
+    host<->device traffic of every pass inside the timed region: each pass
+    resets the forest, and its edges and pairs go to the device and its
+    answers come back. Two ways:
       zero_copy  the bulk calls get the host pointers themselves; the kernels
                  read the edges and pairs and write the answers over the host
                  link (NVLink-C2C on Grace-Blackwell);
@@ -742,28 +859,24 @@ def run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist) -> dict:
     from paper_1602_05232_gb300 import cc
 
     B = s.batches
-    steps = min(args.steps, B)
-    opts = launch_options(args.workload)
+    opts = launch_options(workload)
     h_o = torch.empty(s.q, dtype=torch.uint8, pin_memory=True)
     stream = torch.cuda.Stream(device=dev)
     results = {}
-    h2d = d2h = edges = 0
-    for i in range(steps):
-        b = i % B
-        edges += int(eoff[b + 1] - eoff[b])
-        h2d += 8 * int(eoff[b + 1] - eoff[b]) + 8 * int(qoff[b + 1] - qoff[b])
-        d2h += int(qoff[b + 1] - qoff[b])
+    h2d = 8 * s.m + 8 * s.q                       # per pass (= per step)
+    d2h = s.q
 
-    def timed(run_steps):
+    def timed(run_pass):
         with torch.cuda.stream(stream):
             f = cc.Forest(s.n, stream=stream, **opts)
-            run_steps(f, min(args.warmup, B), warm=True)
-            f.reset()
+            for _ in range(max(1, min(W, 2))):
+                run_pass(f)
             stream.synchronize()
             dist_barrier(dist)
             a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            run_steps(f, steps, warm=False)
+            for _ in range(K):
+                run_pass(f)
             b_.record(stream)
             stream.synchronize()
             dist_barrier(dist)
@@ -773,48 +886,49 @@ def run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist) -> dict:
 
     zero_copy_ok = cc.device_can_read(h_edges) and cc.device_can_read(h_o)
     if zero_copy_ok:
-        def zc(f, n_steps, warm):
-            for i in range(n_steps):
-                b = i % B
-                f.bulk_update(h_edges[eoff[b]:eoff[b + 1]])
-                f.bulk_query(h_pairs[qoff[b]:qoff[b + 1]], out=h_o[qoff[b]:qoff[b + 1]])
+        zviews = [(h_edges[eoff[b]:eoff[b + 1]], h_pairs[qoff[b]:qoff[b + 1]], h_o[qoff[b]:qoff[b + 1]])
+                  for b in range(B)]
+
+        def zc(f):
+            f.reset()
+            for e, q, o in zviews:
+                f.bulk_update(e)
+                f.bulk_query(q, out=o)
         results["zero_copy"] = timed(zc)
 
     copy_in = torch.cuda.Stream(device=dev)
     copy_out = torch.cuda.Stream(device=dev)
 
     def make_piped(G: int):
-        """Steps in groups of G consecutive minibatches: one host->device copy
+        """A pass in groups of G consecutive minibatches: one host->device copy
         of the group's edges and one of its pairs (contiguous ranges of the
         pinned stream), one device->host copy of its answers, two device
         buffers so that a group's copies overlap the previous group's kernels.
-        Every step is still one cc_bulk_update + one cc_bulk_query call. All
-        tensor views are made before the timed region."""
-        groups = [list(range(g, min(g + G, steps))) for g in range(0, steps, G)]
-        ke = max(int(eoff[grp[-1] % B + 1] - eoff[grp[0] % B]) for grp in groups)
-        kq = max(int(qoff[grp[-1] % B + 1] - qoff[grp[0] % B]) for grp in groups)
+        Every minibatch is still one cc_bulk_update + one cc_bulk_query call.
+        All tensor views are made before the timed region."""
+        groups = [list(range(g, min(g + G, B))) for g in range(0, B, G)]
+        ke = max(int(eoff[grp[-1] + 1] - eoff[grp[0]]) for grp in groups)
+        kq = max(int(qoff[grp[-1] + 1] - qoff[grp[0]]) for grp in groups)
         d_e = [torch.empty((ke, 2), dtype=torch.int32, device=dev) for _ in range(2)]
         d_q = [torch.empty((kq, 2), dtype=torch.int32, device=dev) for _ in range(2)]
         d_o = [torch.empty(kq, dtype=torch.uint8, device=dev) for _ in range(2)]
         plan = []
         for gi, grp in enumerate(groups):
             j = gi % 2
-            b0, b1 = grp[0] % B, grp[-1] % B + 1
+            b0, b1 = grp[0], grp[-1] + 1
             ne, nq = int(eoff[b1] - eoff[b0]), int(qoff[b1] - qoff[b0])
             calls = []
-            for i in grp:
-                b = i % B
+            for b in grp:
                 e_lo, e_hi = int(eoff[b] - eoff[b0]), int(eoff[b + 1] - eoff[b0])
                 q_lo, q_hi = int(qoff[b] - qoff[b0]), int(qoff[b + 1] - qoff[b0])
                 calls.append((d_e[j][e_lo:e_hi], d_q[j][q_lo:q_hi], d_o[j][q_lo:q_hi]))
             plan.append((j, h_edges[eoff[b0]:eoff[b1]], d_e[j][:ne], h_pairs[qoff[b0]:qoff[b1]], d_q[j][:nq],
                          h_o[qoff[b0]:qoff[b1]], d_o[j][:nq], calls))
+        done_ev = [torch.cuda.Event(), torch.cuda.Event()]
+        ready_ev = [torch.cuda.Event(), torch.cuda.Event()]
+        out_ev = [torch.cuda.Event(), torch.cuda.Event()]
 
-        def piped(f, n_steps, warm):
-            todo = plan[:1] if warm else plan       # warm-up: the first group only
-            done_ev = [torch.cuda.Event(), torch.cuda.Event()]
-            ready_ev = [torch.cuda.Event(), torch.cuda.Event()]
-            out_ev = [torch.cuda.Event(), torch.cuda.Event()]
+        def piped(f):
             for e in done_ev + out_ev:
                 e.record(stream)
 
@@ -826,9 +940,10 @@ def run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist) -> dict:
                     dq.copy_(hq, non_blocking=True)
                 ready_ev[j].record(copy_in)
 
+            f.reset()
             issue_copy(0)
-            for gi, (j, he, de, hq, dq, ho, do, calls) in enumerate(todo):
-                if gi + 1 < len(todo):
+            for gi, (j, he, de, hq, dq, ho, do, calls) in enumerate(plan):
+                if gi + 1 < len(plan):
                     issue_copy(gi + 1)
                 stream.wait_event(ready_ev[j])
                 stream.wait_event(out_ev[j])        # the answers that used buffer j are out
@@ -846,16 +961,16 @@ def run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist) -> dict:
 
     for G in (1, 2, 4):
         results[f"pipelined_g{G}"] = timed(make_piped(G))
-    edges_all = dist_sum(dist, float(edges), dev)
+    edges_all = dist_sum(dist, float(K * s.m), dev)
     best = min(results, key=results.get)
     return {"value": round(edges_all / (results[best] / 1e3), 1), "unit": "edges/s",
-            "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
-            "steps": steps, "variant": best,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": K, "variant": best,
             "variants": {k: round(edges_all / (v / 1e3), 1) for k, v in results.items()},
-            "what": "pinned host buffers through cc_bulk_update/cc_bulk_query; zero_copy: the "
-                    "kernels read/write host memory directly; pipelined_gG: copies on two copy "
-                    "streams overlapping the kernels, G minibatches per copy (one update and one "
-                    "query call per minibatch)"}
+            "what": "pinned host buffers through cc_bulk_update/cc_bulk_query, one whole pass per "
+                    "step; zero_copy: the kernels read/write host memory directly; pipelined_gG: "
+                    "copies on two copy streams overlapping the kernels, G minibatches per copy "
+                    "(one update and one query call per minibatch)"}
 
 
 # ------------------------------------------------------------ CPU oracle
@@ -908,7 +1023,10 @@ def host_info() -> dict:
 
 
 def run_reference(args, rank: int, world: int) -> dict | None:
-    """--impl reference: the CPU oracle on a bounded sample of every step."""
+    """--impl reference: the CPU oracle, as it stands, on a bounded sample of
+    every step. A step is one pass of the workload's stream from the empty
+    graph, as in the GPU arm, over the first 1/frac of every minibatch's
+    edges and pairs."""
     if rank != 0:
         return None
     import oracle
@@ -916,48 +1034,39 @@ def run_reference(args, rank: int, world: int) -> dict | None:
     B = s.batches
     frac = args.ref_fraction
     eoff, qoff = s.edge_offsets(), s.query_offsets()
-    uf = oracle.OracleUF(s.n)
-    cache = {}
+    sample = []
+    for b in range(B):
+        ke = max(1, int(eoff[b + 1] - eoff[b]) // frac)
+        kq = max(1, int(qoff[b + 1] - qoff[b]) // frac)
+        sample.append((s.edges_range(int(eoff[b]), int(eoff[b]) + ke), uniform_slice(s, b, kq)))
+    edges_per_pass = sum(len(e) for e, _ in sample)
+    pairs_per_pass = sum(len(q) for _, q in sample)
 
-    def batch(b):
-        if b not in cache:
-            ke = max(1, int(eoff[b + 1] - eoff[b]) // frac)
-            kq = max(1, int(qoff[b + 1] - qoff[b]) // frac)
-            cache[b] = (s.edges_range(int(eoff[b]), int(eoff[b]) + ke),
-                        uniform_slice(s, b, kq))
-        return cache[b]
+    def one_pass():
+        uf = oracle.OracleUF(s.n)
+        for e, q in sample:
+            uf.bulk_update(e)
+            uf.bulk_query(q)
 
-    def step(i):
-        nonlocal uf
-        b = i % B
-        if b == 0 and i > 0:
-            uf = oracle.OracleUF(s.n)
-        e, q = batch(b)
-        uf.bulk_update(e)
-        uf.bulk_query(q)
-        return len(e), len(q)
-
-    for i in range(min(B, args.steps)):
-        batch(i % B)
-    for i in range(args.warmup):
-        step(i)
-    uf = oracle.OracleUF(s.n)
+    for _ in range(args.warmup):
+        one_pass()
     t0 = time.perf_counter()
-    edges = 0
-    for i in range(args.steps):
-        k, _ = step(i)
-        edges += k
+    for _ in range(args.steps):
+        one_pass()
     dt = time.perf_counter() - t0
-    v = edges / dt
+    v = args.steps * edges_per_pass / dt
     return {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "edges/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * dt / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "queries_per_s": round(args.steps * pairs_per_pass / dt, 1),
             "config": {"workload": WORKLOAD_TEXT[args.workload],
-                       "sample": f"each step applies the first 1/{frac} of its minibatch's edges "
-                                 f"and queries the first 1/{frac} of its pairs"},
+                       "step": "one pass of the stream from the empty graph",
+                       "sample": f"each pass applies the first 1/{frac} of every minibatch's edges "
+                                 f"and queries the first 1/{frac} of its pairs ({edges_per_pass} "
+                                 f"edges + {pairs_per_pass} pairs per pass)"},
             "cpu_baseline": {"value": round(v, 1), "unit": "edges/s", "cores": 1, "kind": "oracle",
-                             "sample": f"1/{frac} of every minibatch, {args.steps} steps",
+                             "sample": f"1/{frac} of every minibatch, {args.steps} passes",
                              "host_cores_available": os.cpu_count(), "host": host_info()},
             "e2e": {"value": round(v, 1), "unit": "edges/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -968,14 +1077,28 @@ def uniform_slice(s, b: int, kq: int) -> np.ndarray:
     return I.uniform_pairs(s.n, kq, s.seed, I.TAG_QUERIES, int(s.query_offsets()[b]))
 
 
+HEADLINE = "grid"
+FORMS = ("rmat", "uniform", "segmented", "serving")
+DROP_IN_FORMS = ("metric", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "dtype", "data",
+                 "e2e", "cpu_baseline", "warmup")
+
+
+def form_summary(d: dict) -> dict:
+    return {k: v for k, v in d.items() if k not in DROP_IN_FORMS}
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5120)
-    ap.add_argument("--warmup", type=int, default=16)
+    ap.add_argument("--steps", type=int, default=20,
+                    help="timed steps; a step of a plain workload is one whole pass of its stream")
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", choices=sorted(LAUNCH_OPTIONS) + [
-        "paper-random", "paper-rmat5", "paper-rmat16", "paper-3dgrid"], default="rmat")
+        "paper-random", "paper-rmat5", "paper-rmat16", "paper-3dgrid"], default=HEADLINE)
+    ap.add_argument("--forms", default="all",
+                    help="with the headline workload: the other forms to run and report in the same "
+                         "line, a comma list of " + ",".join(FORMS) + ", or 'all' or 'none'")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-fraction", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
@@ -990,6 +1113,11 @@ def main(argv=None) -> int:
     for kv in args.opt:
         k, v = kv.split("=", 1)
         OPTION_OVERRIDES[k] = int(v)
+    forms = [] if args.forms == "none" else list(FORMS) if args.forms == "all" else \
+        [x for x in args.forms.split(",") if x]
+    for x in forms:
+        if x not in FORMS:
+            ap.error(f"--forms: unknown form {x}")
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world)
@@ -1002,7 +1130,27 @@ def main(argv=None) -> int:
         elif args.workload.startswith("paper-"):
             out = run_paper(args, rank, world, local_rank, dist)
         else:
-            out = run_gpu(args, rank, world, local_rank, dist)
+            out = run_gpu(args, rank, world, local_rank, dist, e2e=not args.no_e2e)
+            if args.workload == HEADLINE and forms:
+                sub = {}
+                for x in forms:
+                    if x in ("rmat", "uniform"):
+                        d = run_gpu(args, rank, world, local_rank, dist, workload=x, e2e=False, cpu=False)
+                    elif x == "segmented":
+                        d = run_segmented(args, rank, world, local_rank, dist)
+                    else:
+                        d = run_serving(args, rank, world, local_rank, dist)
+                    if d is not None:
+                        sub[x] = form_summary(d)
+                if out is not None:
+                    out["forms"] = sub
+                    out["forms_what"] = (
+                        "the other configurations in the same run: rmat (plain, R-MAT n=2^24), "
+                        "uniform (plain, n=2^16), segmented (batched form: 1024 graphs in one "
+                        "persistent kernel replayed as a CUDA graph, against one launch per "
+                        "minibatch), serving (served form on R-MAT n=2^26, 2^30 edges: saturation "
+                        "and p50/p99 request latency at 0.5/0.8/0.95 load, against one request at "
+                        "a time)")
         if dist is not None:
             dist.destroy_process_group()
     if rank == 0 and out is not None:

@@ -379,10 +379,10 @@ cc_status cc_kernel_stats(cc_ctx* ctx, uint64_t* launches, double* ms);
 /* ------------------------------------------- allocation-free labelling */
 
 /* The paper has no counterpart to this entry point: it exists for callers
- * that cannot allocate device memory. Examples are code whose stream is being
- * captured into a CUDA graph, real-time loops that cannot afford cudaMalloc's
- * implicit synchronisation, and plugins whose host framework owns all device
- * memory.
+ * that cannot allocate device memory. Examples are real-time loops that
+ * cannot afford cudaMalloc's implicit synchronisation and unbounded latency,
+ * and plugins whose host framework owns all device memory and offers them no
+ * allocator.
  *
  * Computes labels[v] = the smallest vertex id connected to v in the graph of
  * the k edges at `edges` on vertices 0..n-1: one Bulk-Update of a fresh
@@ -397,8 +397,10 @@ cc_status cc_kernel_stats(cc_ctx* ctx, uint64_t* launches, double* ms);
  *
  * All calls share the static array and each call re-initialises it, so calls
  * whose work can overlap on the GPU (e.g. on two unordered streams) race and
- * give wrong labels: order them. The first call on each device looks up the
- * array's device address; make that first call before any stream capture.
+ * give wrong labels: order them. The first call on each device (and the
+ * first after that device's context was replaced, e.g. by cudaDeviceReset)
+ * looks up the array's device address; make that first call before any
+ * stream capture.
  *
  * Errors: CC_ERR_ARG if n < 1 or n > CC_STATIC_MAX_VERTICES, or for bad k or
  * pointers, with nothing enqueued; CC_ERR_CUDA if the lookup or a launch

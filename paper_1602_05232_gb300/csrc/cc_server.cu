@@ -82,6 +82,7 @@ struct cc_server {
     int64_t next_launch = 0, completed = 0, groups = 0;
     int64_t n_upd = 0, n_qry = 0, edges = 0, pairs = 0;
     int64_t head = 0;
+    int64_t used = 0;  // ring pairs held by in-flight groups
     std::deque<Group*> inflight;
     bool stop = false;
     cc_status err = CC_OK;
@@ -115,6 +116,7 @@ void mark_done(cc_server* s, Group* g, double t) {
     g->done = true;
     while (!s->inflight.empty() && s->inflight.front()->done) {
         Group* f = s->inflight.front();
+        s->used -= f->e - f->b;
         s->spare_events.push_back(f->ev);
         delete f;
         s->inflight.pop_front();
@@ -168,26 +170,40 @@ void reaper_loop(cc_server* s) {
 }
 
 // Reserve [b, b+k) of the ring (FIFO). Called with the lock held.
+//
+// Groups take ranges in launch order and free them in the same order, so the
+// occupied part is one arc from the oldest non-empty in-flight group's start
+// (tail) to head, possibly wrapping past the end. Emptiness is decided by the
+// number of pairs held, not by head == tail: a group of zero pairs sits at
+// head without occupying anything, and when it is the oldest in flight while
+// later groups have filled the ring all the way round, head == tail means
+// full.
 bool ring_alloc(cc_server* s, int64_t k, int64_t* b) {
-    if (s->inflight.empty()) s->head = 0;
+    if (s->used == 0) s->head = 0;
     if (k == 0) {
         *b = s->head;
         return true;
     }
-    if (s->inflight.empty()) {
+    if (s->used == 0) {
         if (k > s->cap) return false;
         *b = 0;
         return true;
     }
-    const int64_t tail = s->inflight.front()->b;
-    if (s->head > tail || (s->head == tail && s->inflight.front()->e == tail)) {
-        // used region [tail, head): free space at the end, then at the start
+    int64_t tail = s->head;
+    for (const Group* g : s->inflight)
+        if (g->e > g->b) {
+            tail = g->b;
+            break;
+        }
+    if (s->head > tail) {
+        // occupied [tail, head): free space at the end, then at the start
         if (s->cap - s->head >= k) { *b = s->head; return true; }
         if (tail >= k) { *b = 0; return true; }
         return false;
     }
-    if (s->head < tail && tail - s->head >= k) { *b = s->head; return true; }
-    return false;  // head == tail with work in flight: full
+    // wrapped: occupied [tail, cap) and [0, head); free [head, tail)
+    if (tail - s->head >= k) { *b = s->head; return true; }
+    return false;
 }
 
 
@@ -227,6 +243,7 @@ void worker_loop(cc_server* s) {
             }
             s->inflight.push_back(g);
             s->head = b + total;
+            s->used += total;
             s->next_launch = last;
             s->groups++;
             batch.clear();

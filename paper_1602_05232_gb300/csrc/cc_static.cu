@@ -1,20 +1,20 @@
 // cc_components_static: connected-component labels of one edge list, using
 // no memory that has to be allocated.
 //
-// Callers that cannot call cudaMalloc -- code running while its stream is
-// captured into a CUDA graph, real-time loops that must not take the implicit
-// device synchronisation and unbounded latency of an allocation, and plugins
-// whose host framework owns all device memory and offers them no allocator --
-// can still label a graph: the working forest and the status word live in the
-// file-scope device array below, which is part of the loaded module, not of
-// any allocation. The caller passes only its inputs (the edges) and outputs
-// (the labels, and optionally a status word).
+// Some callers cannot call cudaMalloc: real-time loops that must not take the
+// implicit device synchronisation and unbounded latency of an allocation, and
+// plugins whose host framework owns all device memory and offers them no
+// allocator. They can still label a graph: the working forest and the status
+// word live in the file-scope device array below, which is part of the loaded
+// module, not of any allocation. The caller passes only its inputs (the
+// edges) and outputs (the labels, and optionally a status word).
 //
 // The array holds CC_STATIC_MAX_VERTICES vertices (16 MiB + 256 B) and every
 // GPU that loads this library keeps it until the process exits. All calls
 // share it: each call re-initialises what it uses before its kernels read it,
 // and two calls whose work overlaps on the GPU (different streams, no
 // ordering between them) race on it and give wrong labels.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -33,20 +33,62 @@ static __device__ __align__(256) int32_t g_static_scratch[kHeaderInts + CC_STATI
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-int32_t* g_scratch_ptr[kMaxDevices] = {};
+
+// The address is cached per device together with the id of the context it
+// was looked up in: if that context is destroyed (cudaDeviceReset) and a new
+// one made, the module is loaded again, possibly elsewhere, and the lookup
+// must be repeated. Context ids are never reused within a process.
+struct ScratchAddr {
+    unsigned long long ctx_id = 0;
+    int32_t* ptr = nullptr;
+};
+ScratchAddr g_scratch[kMaxDevices];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Id of the calling thread's current context, or 0 if there is none or the
+// driver cannot say. The two driver calls are reached through the runtime's
+// entry-point query, so libcc does not link the driver library itself.
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 // Device address of the scratch on the current device. In host code the
 // array's name is only a host-side stand-in; the kernels need this address.
-// Looked up once per device (the first call on a device does it).
+// Looked up on the first call on a device (and again only if that device's
+// context has been replaced since); make that first call before any stream
+// capture.
 cudaError_t scratch_address(int device, int32_t** out) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[device]) {
+    ScratchAddr& a = g_scratch[device];
+    const unsigned long long id = current_context_id();
+    if (!a.ptr || id == 0 || id != a.ctx_id) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_ptr[device] = static_cast<int32_t*>(p);
+        a.ptr = static_cast<int32_t*>(p);
+        a.ctx_id = current_context_id();  // the lookup made a context current if none was
     }
-    *out = g_scratch_ptr[device];
+    *out = a.ptr;
     return cudaSuccess;
 }
 

@@ -164,3 +164,20 @@ def test_submit_on_plain_handle(cc):
     for (e, q), o in zip(s, outs):
         ref.bulk_update(e)
         assert np.array_equal(o.cpu().numpy(), ref.bulk_query(q))
+
+
+def test_segmented_full_size_at_the_benchmarked_launch_shape(cc):
+    # the full 1024-graph workload at the launch options the benchmark times
+    # (the tuned CTA size, edges per thread, shared-memory cap and persistent
+    # grid), checked against the oracle, then replayed through the captured
+    # graph on a reset forest and checked again
+    from bench import launch_options
+    opts = launch_options("segmented")
+    w = I.segmented_workload()
+    f = check(cc, w, opts)
+    f.reset()
+    ops, out, qbase, keep = build_ops(cc, w)
+    f.submit(ops)
+    got = out.cpu().numpy()
+    want, _ = oracle_answers(w, qbase)
+    assert np.array_equal(got, want)

@@ -115,6 +115,34 @@ def test_served_equals_alone(cc, mode):
         assert st["groups"] == len(reqs)
 
 
+def test_empty_requests_do_not_hide_a_full_ring(cc):
+    # A request of zero pairs becomes a group that sits at the ring's head
+    # without occupying it. With no merging (one group per request) and a
+    # ring a few groups long, such a group is often the oldest in flight
+    # while later groups wrap all the way round to its position; the ring is
+    # then full, not empty, and a new group must wait. Every answer and the
+    # final labels must still match the oracle run request by request.
+    n, reqs, data = make_trace(scale=14, m=1 << 17, seed=10, ulo=4, uhi=9, qlo=4, qhi=9)
+    rng = np.random.default_rng(10)
+    Req = type(reqs[0])
+    reqs2, data2 = [], []
+    for r, d in zip(reqs, data):
+        if rng.random() < 0.3:
+            kind = int(rng.integers(0, 2))
+            reqs2.append(Req(r.t, kind, 0, 0))
+            data2.append(torch.zeros((0, 2), dtype=torch.int32).pin_memory())
+        reqs2.append(r)
+        data2.append(d)
+    want, want_labels = alone_answers(n, reqs2, data2)
+    for ring in (1 << 10, 1536):
+        got, labels, _, st = serve(cc, n, reqs2, data2, merge=False, ring_pairs=ring,
+                                   max_group_pairs=1 << 9)
+        for i, w in want.items():
+            assert np.array_equal(got[i], w), f"ring {ring}: request {i} differs from running it alone"
+        assert np.array_equal(labels, want_labels)
+        assert st["completed"] == st["requests"] == len(reqs2)
+
+
 def test_served_equals_plain_gpu_alone(cc):
     n, reqs, data = make_trace(scale=14, m=1 << 16, seed=8)
     got, labels, _, _ = serve(cc, n, reqs, data)
@@ -197,3 +225,34 @@ def test_enqueue_many_checks_everything_first(cc):
         srv.drain()
         assert srv.stats()["completed"] == 2 and o[0] == 1     # 1-2 joined by the update before it
     f.close()
+
+
+def test_full_size_served_trace_equals_oracle(cc):
+    # The served workload exactly as the benchmark serves it: R-MAT n = 2^26,
+    # 2^30 edges, Poisson request trace (updates of log-uniform [2^8, 2^20]
+    # edges, queries of log-uniform [2^8, 2^18] pairs, 3:1), all requests handed
+    # over in one call, the tuned serving options and the default staging ring
+    # and group sizes. Every query request's answers, and the final labels,
+    # must equal the oracle's with the requests applied one by one in arrival
+    # order (a query sees exactly the updates before it).
+    from bench import ServingTrace, launch_options
+    tr = ServingTrace(26, seed=0)
+    f = cc.Forest(tr.n, **launch_options("serving"))
+    with cc.Server(f) as srv:
+        srv.enqueue_many(*tr.many)
+        srv.drain()
+        st = srv.stats()
+    labels = f.labels().cpu().numpy()
+    f.sync()
+    f.close()
+    assert st["completed"] == st["requests"] == len(tr.reqs)
+    assert st["groups"] < len(tr.reqs)
+    uf = oracle.OracleUF(tr.n)
+    edges, pairs, got = tr.h_edges.numpy(), tr.h_pairs.numpy(), tr.h_out.numpy()
+    for i, r in enumerate(tr.reqs):
+        if r.kind == 0:
+            uf.bulk_update(edges[r.offset:r.offset + r.size])
+        else:
+            want = uf.bulk_query(pairs[r.offset:r.offset + r.size])
+            assert np.array_equal(got[r.offset:r.offset + r.size], want), f"request {i} differs"
+    assert np.array_equal(labels, uf.labels())
