@@ -141,7 +141,19 @@ typedef enum {
                                     graph is built on the first such update and rebuilt when the A''
                                     buffer grows or the block size changes. 0 = the host reads a
                                     flag after every round. Same answers and labels */
-    CC_OPT__COUNT = 21
+    CC_OPT_EDGE_ORDER = 21,      /* 0 = Bulk-Update takes the edges in the caller's order (default);
+                                    b in 6..9 = it first orders a minibatch of at least 4096 edges
+                                    into 2^b buckets by the smaller endpoint's id (a counting sort
+                                    into a scratch copy; the caller's array is not written), so
+                                    that the update reads the forest in roughly address order. A
+                                    minibatch is a set (Section 1), so the result is the same; on
+                                    graphs whose ids have locality (meshes numbered row by row)
+                                    the forest's lines are then fetched about once per minibatch
+                                    instead of once per endpoint. The scratch (8 B per edge of the
+                                    largest minibatch so far, plus 8 B per bucket) is allocated on
+                                    first use and grown with one stream synchronisation. Counted
+                                    as CC_K_ORDER launches (two per ordered minibatch) */
+    CC_OPT__COUNT = 22
 } cc_option;
 
 /* Kernel kinds reported by the launch counters and the profiler. */
@@ -154,7 +166,8 @@ typedef enum {
     CC_K_RESET = 5,
     CC_K_LOAD = 6,
     CC_K_SEGMENTED = 7,
-    CC_K__COUNT = 8
+    CC_K_ORDER = 8,          /* the locality order of CC_OPT_EDGE_ORDER (count, scan, scatter) */
+    CC_K__COUNT = 9
 } cc_kernel_kind;
 
 /* ------------------------------------------------------------ lifetime */

@@ -51,7 +51,11 @@ struct DeviceScope {
 };
 
 const int64_t kDefaults[CC_OPT__COUNT] = {256, 2, 1, CC_COMPRESS_ALL, 0, 0, 0, 0,
-                                          512, 1, 65536, 1, 0, 0, 0, 0, 0, 1, 0, 0, 1};
+                                          512, 1, 65536, 1, 0, 0, 0, 0, 0, 1, 0, 0, 1, 0};
+
+// Minibatches below this many edges are never reordered (CC_OPT_EDGE_ORDER):
+// their parent reads are too few to share L2 lines.
+constexpr int64_t kOrderMinEdges = 4096;
 
 }  // namespace
 
@@ -103,6 +107,13 @@ struct cc_ctx {
     int64_t live_cap = 0;           // in entries
     unsigned* live_count = nullptr; // the two alternating list counters
     uint64_t live_seq = 0;          // two-pass updates so far (selects the counter)
+
+    // locality order of the edges (CC_OPT_EDGE_ORDER)
+    int* order_buf = nullptr;       // the ordered copy of a minibatch (2 ints per edge)
+    int64_t order_cap = 0;          // in edges
+    int* order_hist = nullptr;      // bucket totals, fill counters and a done counter
+    int64_t order_hist_cap = 0;     // in ints
+    bool order_dirty = false;       // a failed launch may have left the counters non-zero
 
     // union by size (CC_OPT_LINK = 1)
     int* size = nullptr;                 // tree sizes, meaningful at roots
@@ -192,7 +203,7 @@ cc::Launch update_cfg(const cc_ctx* c, bool first) {
 
 // One Bulk-Update as a filter pass and a live-edge pass (update variant 4).
 // The list has room for k entries; growing it synchronises the stream once.
-cc_status split_update(cc_ctx* c, const int32_t* edges, int64_t k, bool first) {
+cc_status split_update(cc_ctx* c, const int32_t* edges, int64_t k, bool first, bool ordered) {
     cudaError_t e = cudaSuccess;
     if (!c->live_count) {
         e = cudaMalloc(&c->live_count, 2 * sizeof(unsigned));
@@ -217,14 +228,66 @@ cc_status split_update(cc_ctx* c, const int32_t* edges, int64_t k, bool first) {
         c->live_cap = k;
     }
     const int sel = (int)(c->live_seq & 1u);
+    cc::Launch cfg = update_cfg(c, first);
+    if (ordered && cfg.pdl == 2) cfg.pdl = 1;  // its edges were written by the kernel just before
     cc_status s = run(c, CC_K_UPDATE, "bulk_update (two passes)", [&] {
-        return cc::launch_update_split(c->parent, (int)c->n, edges, k, c->ds, update_cfg(c, first), c->live,
+        return cc::launch_update_split(c->parent, (int)c->n, edges, k, c->ds, cfg, c->live,
                                        c->live_count, sel, c->stream);
     });
     if (s == CC_OK) {
         c->live_seq++;
         c->launches[CC_K_UPDATE]++;  // the second kernel
     }
+    return s;
+}
+
+// CC_OPT_EDGE_ORDER: the minibatch bucketed by its smaller endpoints into the
+// handle's scratch copy, which then replaces `edges` for the update. The
+// scratch grows to the largest minibatch with one stream synchronisation;
+// its bucket counters start at zero and every call leaves them at zero.
+cc_status order_edges(cc_ctx* c, const int32_t** edges, int64_t k) {
+    const int b = (int)c->opt[CC_OPT_EDGE_ORDER];
+    const int64_t counters = cc::order_counter_ints(b);
+    if (k > c->order_cap || counters > c->order_hist_cap || c->order_dirty) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "edge order: sync");
+        if (k > c->order_cap) {
+            int* q = nullptr;
+            e = cudaMalloc(&q, sizeof(int) * 2 * (size_t)k);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(CC_ERR_OOM, "edge order: copy of %lld edges", (long long)k);
+            }
+            cudaFree(c->order_buf);
+            c->order_buf = q;
+            c->order_cap = k;
+        }
+        if (counters > c->order_hist_cap) {
+            int* q = nullptr;
+            e = cudaMalloc(&q, sizeof(int) * (size_t)counters);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(CC_ERR_OOM, "edge order: bucket counters");
+            }
+            cudaFree(c->order_hist);
+            c->order_hist = q;
+            c->order_hist_cap = counters;
+        }
+        e = cudaMemsetAsync(c->order_hist, 0, sizeof(int) * (size_t)c->order_hist_cap, c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "edge order: clear counters");
+        c->order_dirty = false;
+    }
+    int kernels = 1;
+    cc_status s = run(c, CC_K_ORDER, "edge order", [&] {
+        return cc::launch_order_edges(*edges, k, (int)c->n, b, c->order_hist, c->order_buf,
+                                      (int)c->opt[CC_OPT_PDL], c->stream, &kernels);
+    });
+    if (s != CC_OK) {
+        c->order_dirty = true;  // the counters may be left non-zero
+        return s;
+    }
+    c->launches[CC_K_ORDER] += kernels - 1;  // run() counted one
+    *edges = c->order_buf;
     return s;
 }
 
@@ -472,6 +535,8 @@ cc_status cc_destroy(cc_ctx* c) {
         cudaFree(c->best);
         cudaFree(c->live);
         cudaFree(c->live_count);
+        cudaFree(c->order_buf);
+        cudaFree(c->order_hist);
         cc::bulk_find_free(c->bf);
         cudaFree(c->parent);
         cudaFree(c->ds);
@@ -533,14 +598,22 @@ cc_status cc_bulk_update(cc_ctx* c, const int32_t* edges, int64_t k) {
     if (by_size(c) && c->opt[CC_OPT_UPDATE_SCHEDULE] != 1)
         return fail(CC_ERR_UNSUPPORTED, "union by size (CC_OPT_LINK = 1) needs CC_OPT_UPDATE_SCHEDULE = 1");
     const bool first = c->fresh;  // the forest has no edge yet
+    bool ordered = false;
+    if (c->opt[CC_OPT_EDGE_ORDER] > 0 && k >= kOrderMinEdges) {
+        s = order_edges(c, &edges, k);
+        if (s != CC_OK) return s;
+        ordered = true;
+    }
     c->fresh = false;
     if (c->opt[CC_OPT_UPDATE_SCHEDULE] == 1) {
         s = paper_update(c, edges, k);
     } else if (c->opt[CC_OPT_UPDATE_VARIANT] == 4) {
-        s = split_update(c, edges, k, first);
+        s = split_update(c, edges, k, first, ordered);
     } else {
+        cc::Launch cfg = update_cfg(c, first);
+        if (ordered && cfg.pdl == 2) cfg.pdl = 1;  // its edges were written by the kernel just before
         s = run(c, CC_K_UPDATE, "bulk_update", [&] {
-            return cc::launch_update(c->parent, (int)c->n, edges, k, c->ds, update_cfg(c, first), c->stream);
+            return cc::launch_update(c->parent, (int)c->n, edges, k, c->ds, cfg, c->stream);
         });
     }
     if (s != CC_OK) return s;
@@ -957,6 +1030,10 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
         }
         case CC_OPT_UPDATE_SCHEDULE:
             if (value != 0 && value != 1) return fail(CC_ERR_ARG, "update schedule %lld: need 0 or 1", (long long)value);
+            break;
+        case CC_OPT_EDGE_ORDER:
+            if (value != 0 && (value < 6 || value > 9))
+                return fail(CC_ERR_ARG, "edge order %lld: need 0 (off) or 6..9 (log2 of the bucket count)", (long long)value);
             break;
         case CC_OPT_UPDATE_VARIANT:
             if (value < 0 || value > 4) return fail(CC_ERR_ARG, "update variant %lld: need 0..4", (long long)value);

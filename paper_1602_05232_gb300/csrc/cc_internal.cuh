@@ -74,6 +74,18 @@ cudaError_t launch_compress_all(int* parent, int64_t n, int* out, DevState* ds, 
 cudaError_t launch_compress_touched(int* parent, int n, const int* edges, int64_t k,
                                     DevState* ds, Launch cfg, cudaStream_t s);
 
+// ---- locality order of a Bulk-Update's edges (CC_OPT_EDGE_ORDER) ----
+
+// out (2k ints) = the k edges bucketed by (min endpoint) >> order_shift(n, b)
+// into 2^b buckets (b <= 9). counters: order_counter_ints(b) ints, all zero
+// before the first call; each call leaves them zero again. pdl as for the
+// update kernel (programmatic dependent launch: 0 off, 1 wait first, 2 read
+// the edges first). *kernels = the number of kernels launched.
+int order_shift(int64_t n, int log_buckets);
+int64_t order_counter_ints(int log_buckets);
+cudaError_t launch_order_edges(const int* edges, int64_t k, int n, int log_buckets, int* counters,
+                               int* out, int pdl, cudaStream_t s, int* kernels);
+
 // ---- batched form (segmented forests, one persistent kernel) ----
 
 // One bulk operation of the batched form, as the kernel reads it.

@@ -58,6 +58,15 @@ OPTION_SETS = {
                              "query_halving": 1},
     "pdl_early_query_persistent": {"pdl": 2, "query_variant": 1, "compress_every": 0, "l2_persist": 1},
     "pdl_early_ept1": {"pdl": 2, "update_variant": 1, "edges_per_thread": 1, "compress_every": 2},
+    "order8": {"edge_order": 8},
+    "order6": {"edge_order": 6, "pdl": 2, "compress_every": 0},
+    "order9_persistent_pdl2": {"edge_order": 9, "update_variant": 2, "edges_per_thread": 1, "block": 128,
+                                "pdl": 2, "compress_every": 2},
+    "order7_deep_min_hook": {"edge_order": 7, "update_variant": 3, "edges_per_thread": 2, "hook": 2,
+                              "pdl": 2, "compress_every": 0},
+    "order9_two_pass": {"edge_order": 9, "update_variant": 4, "edges_per_thread": 2, "pdl": 2,
+                         "compress_every": 4},
+    "order8_paper_schedule": {"edge_order": 8, "update_schedule": 1},
 }
 
 
@@ -116,7 +125,8 @@ def test_uniform_small_every_batch(cc, opts):
                                   "lockstep_ept4_nocompress", "persistent_ept4",
                                   "persistent_query_halving", "splitting_query", "deep_prefetch_ept2_pdl2",
                                   "two_pass_ept4", "query_ept2_update_ept4", "min_hook", "min_hook_persistent",
-                                  "min_hook_deep", "min_hook_two_pass", "min_hook_first_only"])
+                                  "min_hook_deep", "min_hook_two_pass", "min_hook_first_only", "order8",
+                                  "order6", "order7_deep_min_hook", "order8_paper_schedule"])
 def test_rmat_small(cc, opts):
     s = I.rmat_stream(scale=16, m=1 << 20, batch=(1 << 16) + 3, q=(1 << 16) - 5, seed=1)
     run_stream(cc, s, OPTION_SETS[opts], label_every=4, check_invariants=True)
@@ -125,7 +135,7 @@ def test_rmat_small(cc, opts):
 @pytest.mark.parametrize("opts", ["default", "no_compress", "ept4_b1024", "compress_every3",
                                   "lockstep", "persistent_ept1_b1024", "splitting_query",
                                   "deep_prefetch_ept1_b1024", "two_pass_ept1_pdl0", "min_hook",
-                                  "min_hook_deep"])
+                                  "min_hook_deep", "order8", "order9_persistent_pdl2", "order9_two_pass"])
 def test_grid_small(cc, opts):
     s = I.grid_stream(512, 512, batch=(1 << 14) + 1, q=1 << 14, seed=2)
     ref = run_stream(cc, s, OPTION_SETS[opts], label_every=8, check_invariants=True)
@@ -201,6 +211,35 @@ def test_out_of_range_ids(cc):
         f.sync()
 
 
+@pytest.mark.parametrize("log_buckets", [6, 8, 9])
+def test_edge_order_ragged_sizes_and_bad_ids(cc, log_buckets):
+    # minibatch sizes around the ordering threshold (4096 edges) and around
+    # the per-CTA chunk granularity, with ids outside [0, n) among the edges:
+    # the ordered copy holds every edge once, bad ones are skipped and
+    # reported, and answers and labels match the oracle
+    n = 70001
+    rng = np.random.default_rng(log_buckets)
+    f = cc.Forest(n, edge_order=log_buckets, compress_every=0)
+    ref = oracle.OracleUF(n)
+    launches0 = f.kernel_stats()["order"]
+    ordered = 0
+    for k in (4095, 4096, 4097, 2047 * 4 + 3, 100003, 262145):
+        e = rng.integers(0, n, size=(k, 2)).astype(np.int32)
+        e[rng.integers(0, k, size=5), rng.integers(0, 2, size=5)] = [-1, n, 2**31 - 1, -7, n + 5]
+        f.bulk_update(dev(e))
+        ref.bulk_update(e)
+        ordered += k >= 4096
+        with pytest.raises(cc.CCError) as ex:
+            f.sync()
+        assert ex.value.status == cc.CC_ERR_RANGE
+        q = rng.integers(0, n, size=(30011, 2)).astype(np.int32)
+        assert np.array_equal(f.bulk_query(dev(q)).cpu().numpy(), ref.bulk_query(q)), k
+    assert f.kernel_stats()["order"] - launches0 == 2 * ordered      # count, scatter
+    assert np.array_equal(f.labels().cpu().numpy(), ref.labels())
+    assert f.components() == ref.components
+    f.sync()
+
+
 def test_argument_errors_leave_state(cc):
     f = cc.Forest(10)
     with pytest.raises(TypeError):
@@ -230,6 +269,7 @@ OPTION_RANGES = [
     ("bulk_find", [2], [0, 1]),
     ("update_schedule", [2], [0, 1]),
     ("sv_graph", [-1, 2], [0, 1]),
+    ("edge_order", [-1, 1, 5, 10], [0, 6, 9]),
 ]
 
 
