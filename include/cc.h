@@ -116,7 +116,11 @@ typedef enum {
                                     Synchronises once per tree level. Default 0 */
     CC_OPT_QUERY_VARIANT = 16,   /* Bulk-Query kernel: 0 = one chunk of pairs per thread (default),
                                     1 = a persistent grid that loads the next chunk's pairs while
-                                    working on the current one */
+                                    working on the current one, 2 = warp-cooperative: a warp takes
+                                    chunks of pairs, each lane keeps two pairs in flight, and a
+                                    ballot hands the next pair of the chunk to every slot whose
+                                    walk has finished (read-only walks whatever
+                                    CC_OPT_QUERY_HALVING says) */
     CC_OPT_PDL = 17,             /* programmatic dependent launch of the Bulk-Update and Bulk-Query
                                     kernels: 0 = off; 1 = each may become resident while the kernel
                                     before it on the stream drains, and waits for that kernel to
@@ -153,7 +157,14 @@ typedef enum {
                                     largest minibatch so far, plus 8 B per bucket) is allocated on
                                     first use and grown with one stream synchronisation. Counted
                                     as CC_K_ORDER launches (two per ordered minibatch) */
-    CC_OPT__COUNT = 22
+    CC_OPT_HOOK_WARP = 22,       /* 1 = the fused Bulk-Update's lockstep variants (CC_OPT_UPDATE_VARIANT
+                                    1..4) group the hooks of a warp by target root: one lane per
+                                    distinct target writes it (compare-and-swap or atomicMin, per
+                                    CC_OPT_HOOK), the others join their smaller root with the
+                                    winner's, so a root that many edges of a minibatch hook onto
+                                    sees one atomic per warp instead of one per edge. 0 = every
+                                    lane hooks on its own (default). Same answers and labels */
+    CC_OPT__COUNT = 23
 } cc_option;
 
 /* Kernel kinds reported by the launch counters and the profiler. */

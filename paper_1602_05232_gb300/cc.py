@@ -28,7 +28,8 @@ OPTIONS = {"block": OPT_BLOCK, "edges_per_thread": OPT_EDGES_PER_THREAD,
            "seg_block": 8, "seg_edges_per_thread": 9, "seg_smem_cap": 10, "seg_graph": 11,
            "seg_max_ctas": 12, "update_schedule": 13, "link": 14,
            "bulk_find": 15, "query_variant": 16, "pdl": 17,
-           "query_pairs_per_thread": 18, "hook": 19, "sv_graph": 20, "edge_order": 21}
+           "query_pairs_per_thread": 18, "hook": 19, "sv_graph": 20, "edge_order": 21,
+           "hook_warp": 22}
 OP_UPDATE, OP_QUERY = 0, 1
 # Layout of cc_op (include/cc.h): graph, kind, data pointer, k, out pointer.
 OP_DTYPE = np.dtype([("graph", "<i4"), ("kind", "<i4"), ("data", "<u8"), ("k", "<i8"),

@@ -51,7 +51,7 @@ struct DeviceScope {
 };
 
 const int64_t kDefaults[CC_OPT__COUNT] = {256, 2, 1, CC_COMPRESS_ALL, 0, 0, 0, 0,
-                                          512, 1, 65536, 1, 0, 0, 0, 0, 0, 1, 0, 0, 1, 0};
+                                          512, 1, 65536, 1, 0, 0, 0, 0, 0, 1, 0, 0, 1, 0, 0};
 
 // Minibatches below this many edges are never reordered (CC_OPT_EDGE_ORDER):
 // their parent reads are too few to share L2 lines.
@@ -161,7 +161,8 @@ cc::Launch cfg_of(const cc_ctx* c) {
     return cc::Launch{(int)c->opt[CC_OPT_BLOCK], (int)c->opt[CC_OPT_EDGES_PER_THREAD],
                       (int)c->opt[CC_OPT_UPDATE_VARIANT], (int)c->opt[CC_OPT_QUERY_VARIANT],
                       c->window.num_bytes > 0 ? &c->window : nullptr, (int)c->opt[CC_OPT_PDL],
-                      (int)c->opt[CC_OPT_QUERY_PAIRS_PER_THREAD], (int)(c->opt[CC_OPT_HOOK] == 1)};
+                      (int)c->opt[CC_OPT_QUERY_PAIRS_PER_THREAD], (int)(c->opt[CC_OPT_HOOK] == 1),
+                      (int)c->opt[CC_OPT_HOOK_WARP]};
 }
 
 cc_status check_pairs(const int32_t* p, int64_t k, const char* name) {
@@ -1010,6 +1011,8 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
             if (value < 0 || value > (1 << 20)) return fail(CC_ERR_ARG, "seg max ctas %lld out of range", (long long)value);
             break;
         case CC_OPT_QUERY_VARIANT:
+            if (value < 0 || value > 2) return fail(CC_ERR_ARG, "query variant %lld: need 0, 1 or 2", (long long)value);
+            break;
         case CC_OPT_BULK_FIND:
             if (value != 0 && value != 1) return fail(CC_ERR_ARG, "option %d takes 0 or 1", option);
             break;
@@ -1030,6 +1033,9 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
         }
         case CC_OPT_UPDATE_SCHEDULE:
             if (value != 0 && value != 1) return fail(CC_ERR_ARG, "update schedule %lld: need 0 or 1", (long long)value);
+            break;
+        case CC_OPT_HOOK_WARP:
+            if (value != 0 && value != 1) return fail(CC_ERR_ARG, "option %d takes 0 or 1", option);
             break;
         case CC_OPT_EDGE_ORDER:
             if (value != 0 && (value < 6 || value > 9))

@@ -107,6 +107,79 @@ __device__ __forceinline__ int hook_as(int* parent, int ru, int rv, DevState* ds
     return minhook ? hook_min(parent, ru, rv, ds) : hook(parent, ru, rv, ds);
 }
 
+// The hooks of a whole warp, grouped by target. Must be called by all 32
+// lanes together. Lane l joins roots-or-former-roots a[i], b[i] for every i
+// with want[i]. In each round the lanes whose larger root `hi` is the same
+// form a group (__match_any_sync): only one lane of the group -- the one
+// with the smallest `lo` -- writes parent[hi], with a compare-and-swap
+// (hook) or an atomicMin (hook_min), instead of every lane of the group
+// contending for that word. Then:
+//  - the write linked hi under lo_min: the leader is done, and every other
+//    member joins its own lo with lo_min (hi is now in lo_min's tree);
+//  - compare-and-swap failed (hi is no longer a root): the leader finds the
+//    root r of hi's new parent once, and every member continues with
+//    (r, its lo);
+//  - atomicMin found hi under old < hi: the leader continues joining old
+//    and lo_min (as hook_min does), every other member joins its lo with
+//    lo_min.
+// Every continuing pair has both ids below hi, so each lane's larger id
+// strictly decreases from round to round and the loop ends. Returns the
+// links this lane made (a write at a root counts once).
+template <int E>
+__device__ __forceinline__ int hook_warp(int* parent, const bool (&want0)[E], const int (&a0)[E],
+                                         const int (&b0)[E], DevState* ds, int minhook) {
+    const unsigned full = 0xffffffffu;
+    const int lane = (int)(threadIdx.x & 31u);
+    int made = 0;
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        bool want = want0[i];
+        int a = a0[i], b = b0[i];
+        while (__any_sync(full, want)) {
+            int hi = a > b ? a : b, lo = a > b ? b : a;
+            if (want && hi == lo) want = false;
+            const unsigned m = __match_any_sync(full, want ? hi : -1 - lane);
+            if (!want) continue;
+            const int lo_min = __reduce_min_sync(m, lo);
+            const int leader = __ffs(__ballot_sync(m, lo == lo_min)) - 1;
+            int old = 0;
+            if (lane == leader)
+                old = minhook ? atomicMin(parent + hi, lo_min) : atomicCAS(parent + hi, hi, lo_min);
+            old = __shfl_sync(m, old, leader);
+            if (old > hi) {  // broken invariant: stop rather than loop
+                if (lane == leader) flag(ds, ST_CORRUPT);
+                want = false;
+            } else if (old == hi) {  // linked hi under lo_min
+                if (lane == leader) {
+                    made++;
+                    want = false;
+                } else {
+                    a = lo;
+                    b = lo_min;
+                }
+            } else if (minhook) {  // hi was already under old
+                if (lane == leader) {
+                    if (old == lo_min) {
+                        want = false;
+                    } else {
+                        a = find_halving(parent, old, ds);
+                        b = find_halving(parent, lo_min, ds);
+                    }
+                } else {
+                    a = lo;
+                    b = lo_min;
+                }
+            } else {  // compare-and-swap failed: hi is no longer a root
+                int r = 0;
+                if (lane == leader) r = find_halving(parent, old, ds);
+                a = __shfl_sync(m, r, leader);
+                b = lo;
+            }
+        }
+    }
+    return made;
+}
+
 // Walk W chains to their roots in lockstep with path splitting. Chain c is at
 // node x[c] whose parent p[c] has been read; it is finished when p[c] >= x[c]
 // (p == x: x is the root). Each round reads the grandparent of every

@@ -36,6 +36,7 @@ struct Launch {
     int pdl = 0;  // programmatic dependent launch: 0 off, 1 wait first, 2 first pairs before the wait
     int qept = 0; // pairs per thread of the query kernel (0 = ept)
     int minhook = 0;  // 1: Bulk-Update hooks with atomicMin + repair (hook_min) instead of CAS
+    int warphook = 0; // 1: the hooks of a warp are grouped by target root (hook_warp); lockstep variants
 };
 
 // Alignment class of a pair array: 2 = 16-byte, 1 = 8-byte, 0 = 4-byte.

@@ -103,7 +103,7 @@ cudaError_t launch_reset(int* parent, int64_t n, int block, cudaStream_t s) {
 // walked to their roots -- VARIANT 0 one edge at a time with path halving,
 // VARIANTs 1 and 2 all 2E walks in lockstep with path splitting -- and the
 // roots are hooked. Returns the number of links made.
-template <int E, int VARIANT>
+template <int E, int VARIANT, bool WARP = false>
 __device__ __forceinline__ int update_edges(int* __restrict__ parent, int n,
                                             const int (&u)[E], const int (&v)[E], int64_t e0,
                                             int64_t k, DevState* __restrict__ ds, int minhook) {
@@ -154,6 +154,15 @@ __device__ __forceinline__ int update_edges(int* __restrict__ parent, int n,
             }
         }
         walk_split<2 * E>(parent, x, p, ds);
+        if constexpr (WARP) {  // every lane of the warp is here (see the kernels)
+            int a[E], b[E];
+#pragma unroll
+            for (int i = 0; i < E; i++) {
+                a[i] = x[2 * i];
+                b[i] = x[2 * i + 1];
+            }
+            return hook_warp<E>(parent, live, a, b, ds, minhook);
+        }
 #pragma unroll
         for (int i = 0; i < E; i++)
             if (live[i]) made += hook_as(parent, x[2 * i], x[2 * i + 1], ds, minhook);
@@ -163,7 +172,10 @@ __device__ __forceinline__ int update_edges(int* __restrict__ parent, int n,
 
 // early: the first edges are read before the wait for the previous kernel
 // (programmatic dependent launch; see launch_windowed), else after it.
-template <int E, int VARIANT>
+// warphook (lockstep variants only): the hooks of a warp are grouped by
+// target (hook_warp), so every lane of a warp that has any edge left goes
+// through each round of the loop, with no edges of its own if it has none.
+template <int E, int VARIANT, bool WARP>
 __global__ void __launch_bounds__(1024)
 k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
          DevState* __restrict__ ds, int early, int minhook) {
@@ -172,11 +184,14 @@ k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t
     int made = 0;
     int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
     if (VARIANT < 2) {
-        if (e0 < k) {
+        // with warphook, every lane goes in if any lane of its warp has edges
+        bool warp_busy = false;
+        if constexpr (WARP) warp_busy = __any_sync(0xffffffffu, e0 < k);
+        if (e0 < k || warp_busy) {
             int u[E], v[E];
             load_pairs<E>(edges, e0, k, vec, u, v);
             if (early) pdl_wait();
-            made = update_edges<E, VARIANT>(parent, n, u, v, e0, k, ds, minhook);
+            made = update_edges<E, VARIANT, WARP>(parent, n, u, v, e0, k, ds, minhook);
         }
     } else {
         // persistent grid: loop over chunks, loading the next chunk's edges
@@ -185,11 +200,11 @@ k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t
         int u[E], v[E];
         if (e0 < k) load_pairs<E>(edges, e0, k, vec, u, v);
         if (early) pdl_wait();
-        while (e0 < k) {
+        while (WARP ? __any_sync(0xffffffffu, e0 < k) : e0 < k) {
             const int64_t nx = e0 + stride;
             int nu[E] = {}, nv[E] = {};
             if (nx < k) load_pairs<E>(edges, nx, k, vec, nu, nv);
-            made += update_edges<E, 1>(parent, n, u, v, e0, k, ds, minhook);
+            made += update_edges<E, 1, WARP>(parent, n, u, v, e0, k, ds, minhook);
 #pragma unroll
             for (int i = 0; i < E; i++) {
                 u[i] = nu[i];
@@ -239,7 +254,7 @@ __device__ __forceinline__ void gather_parents(const int* parent, unsigned m, co
 // is still an ancestor now (links only put roots under roots, and splitting
 // only repoints a node at an ancestor), so walking on from it reaches the
 // current root, and equal values still prove the endpoints joined.
-template <int E>
+template <int E, bool WARP = false>
 __device__ __forceinline__ int walk_and_hook(int* parent, unsigned m, const int (&u)[E], const int (&v)[E],
                                              const int (&pu)[E], const int (&pv)[E], DevState* ds,
                                              int minhook) {
@@ -254,6 +269,15 @@ __device__ __forceinline__ int walk_and_hook(int* parent, unsigned m, const int 
         p[2 * i + 1] = live[i] ? pv[i] : v[i];
     }
     walk_split<2 * E>(parent, x, p, ds);
+    if constexpr (WARP) {  // every lane of the warp is here (see the kernels)
+        int a[E], b[E];
+#pragma unroll
+        for (int i = 0; i < E; i++) {
+            a[i] = x[2 * i];
+            b[i] = x[2 * i + 1];
+        }
+        return hook_warp<E>(parent, live, a, b, ds, minhook);
+    }
     int made = 0;
 #pragma unroll
     for (int i = 0; i < E; i++)
@@ -265,7 +289,7 @@ __device__ __forceinline__ int walk_and_hook(int* parent, unsigned m, const int 
 // hooks of chunk c run, the first parent reads of chunk c+1 and the edge
 // loads of chunk c+2 are already in flight, so a warp waiting on its deepest
 // walk still has the next chunk's gathers outstanding. early: as for k_update.
-template <int E>
+template <int E, bool WARP>
 __global__ void __launch_bounds__(1024)
 k_update_deep(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
               DevState* __restrict__ ds, int early, int minhook) {
@@ -281,14 +305,14 @@ k_update_deep(int* __restrict__ parent, int n, const int* __restrict__ edges, in
     unsigned m0 = e0 < k ? edge_mask<E>(n, u0, v0, e0, k, ds) : 0u;
     int pu0[E], pv0[E];
     gather_parents<E>(parent, m0, u0, v0, pu0, pv0);
-    while (e0 < k) {
+    while (WARP ? __any_sync(0xffffffffu, e0 < k) : e0 < k) {
         const int64_t e1 = e0 + stride, e2 = e1 + stride;
         const unsigned m1 = e1 < k ? edge_mask<E>(n, u1, v1, e1, k, ds) : 0u;
         int pu1[E], pv1[E];
         gather_parents<E>(parent, m1, u1, v1, pu1, pv1);
         int u2[E] = {}, v2[E] = {};
         if (e2 < k) load_pairs<E>(edges, e2, k, vec, u2, v2);
-        made += walk_and_hook<E>(parent, m0, u0, v0, pu0, pv0, ds, minhook);
+        made += walk_and_hook<E, WARP>(parent, m0, u0, v0, pu0, pv0, ds, minhook);
 #pragma unroll
         for (int i = 0; i < E; i++) {
             u0[i] = u1[i]; v0[i] = v1[i]; pu0[i] = pu1[i]; pv0[i] = pv1[i];
@@ -304,12 +328,19 @@ k_update_deep(int* __restrict__ parent, int n, const int* __restrict__ edges, in
 template <int E>
 static void update_deep_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
                              int block, const cudaAccessPolicyWindow* window, int pdl, int minhook,
-                             cudaStream_t s) {
+                             int warphook, cudaStream_t s) {
     int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
-    const int64_t cap = resident_grid<k_update_deep<E>>(block);
+    if (warphook) {
+        const int64_t cap = resident_grid<k_update_deep<E, true>>(block);
+        if (g > cap) g = cap;
+        launch_windowed(k_update_deep<E, true>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k,
+                        vec, ds, (int)(pdl == 2), minhook);
+        return;
+    }
+    const int64_t cap = resident_grid<k_update_deep<E, false>>(block);
     if (g > cap) g = cap;
-    launch_windowed(k_update_deep<E>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k, vec, ds,
-                    (int)(pdl == 2), minhook);
+    launch_windowed(k_update_deep<E, false>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k, vec,
+                    ds, (int)(pdl == 2), minhook);
 }
 
 // --- VARIANT 4: filter pass + live-edge pass ------------------------------
@@ -364,6 +395,7 @@ k_update_filter(const int* __restrict__ parent, int n, const int* __restrict__ e
 }
 
 // Pass 2: two listed edges per thread per step, their four walks in lockstep.
+template <bool WARP>
 __global__ void __launch_bounds__(1024)
 k_update_live(int* __restrict__ parent, const int4* __restrict__ live, const unsigned* __restrict__ count,
               int sel, DevState* __restrict__ ds, int minhook) {
@@ -372,12 +404,14 @@ k_update_live(int* __restrict__ parent, const int4* __restrict__ live, const uns
     const int64_t m = count[sel];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * 2;
     int made = 0;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2; i < m; i += stride) {
-        const int4 a = live[i];
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
+         WARP ? __any_sync(0xffffffffu, i < m) : i < m; i += stride) {
+        const int4 zero = make_int4(0, 0, 0, 0);
+        const int4 a = i < m ? live[i] : zero;
         const int4 b = i + 1 < m ? live[i + 1] : a;
-        const unsigned on = i + 1 < m ? 3u : 1u;
+        const unsigned on = i + 1 < m ? 3u : i < m ? 1u : 0u;
         const int u[2] = {a.x, b.x}, v[2] = {a.y, b.y}, pu[2] = {a.z, b.z}, pv[2] = {a.w, b.w};
-        made += walk_and_hook<2>(parent, on, u, v, pu, pv, ds, minhook);
+        made += walk_and_hook<2, WARP>(parent, on, u, v, pu, pv, ds, minhook);
     }
     made = __reduce_add_sync(0xffffffffu, made);
     if ((threadIdx.x & 31) == 0 && made) atomicAdd(&ds->unions, (unsigned long long)made);
@@ -406,32 +440,50 @@ cudaError_t launch_update_split(int* parent, int n, const int* edges, int64_t k,
     if (e != cudaSuccess) return e;
     // pass 2 on a grid of resident CTAs, capped by the most it could have to do
     int64_t g = (k + 2LL * cfg.block - 1) / (2LL * cfg.block);
-    const int64_t cap = resident_grid<k_update_live>(cfg.block);
-    if (g > cap) g = cap;
-    launch_windowed(k_update_live, (unsigned)g, cfg.block, s, cfg.window, cfg.pdl != 0, parent,
-                    (const int4*)live, (const unsigned*)count, sel, ds, cfg.minhook);
+    if (cfg.warphook) {
+        const int64_t cap = resident_grid<k_update_live<true>>(cfg.block);
+        if (g > cap) g = cap;
+        launch_windowed(k_update_live<true>, (unsigned)g, cfg.block, s, cfg.window, cfg.pdl != 0, parent,
+                        (const int4*)live, (const unsigned*)count, sel, ds, cfg.minhook);
+    } else {
+        const int64_t cap = resident_grid<k_update_live<false>>(cfg.block);
+        if (g > cap) g = cap;
+        launch_windowed(k_update_live<false>, (unsigned)g, cfg.block, s, cfg.window, cfg.pdl != 0, parent,
+                        (const int4*)live, (const unsigned*)count, sel, ds, cfg.minhook);
+    }
     return cudaGetLastError();
 }
 
 
+template <int E, int VARIANT, bool WARP>
+static void update_inst2(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
+                         int block, const cudaAccessPolicyWindow* window, int pdl, int minhook,
+                         cudaStream_t s) {
+    int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
+    if (VARIANT == 2) {
+        const int64_t cap = resident_grid<k_update<E, VARIANT, WARP>>(block);
+        if (g > cap) g = cap;
+    }
+    launch_windowed(k_update<E, VARIANT, WARP>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k,
+                    vec, ds, (int)(pdl == 2), minhook);
+}
+
+// warphook applies to the lockstep variants (1, 2); variant 0 hooks per edge
 template <int E, int VARIANT>
 static void update_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
                         int block, const cudaAccessPolicyWindow* window, int pdl, int minhook,
-                        cudaStream_t s) {
-    int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
-    if (VARIANT == 2) {
-        const int64_t cap = resident_grid<k_update<E, VARIANT>>(block);
-        if (g > cap) g = cap;
-    }
-    launch_windowed(k_update<E, VARIANT>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k, vec, ds,
-                    (int)(pdl == 2), minhook);
+                        int warphook, cudaStream_t s) {
+    if (VARIANT != 0 && warphook)
+        update_inst2<E, VARIANT, VARIANT != 0>(edges, k, vec, parent, n, ds, block, window, pdl, minhook, s);
+    else
+        update_inst2<E, VARIANT, false>(edges, k, vec, parent, n, ds, block, window, pdl, minhook, s);
 }
 
 cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevState* ds,
                           Launch cfg, cudaStream_t s) {
     if (k <= 0) return cudaSuccess;
     const int vec = pair_vec(edges);
-#define CC_UPD(E, V) update_inst<E, V>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, s)
+#define CC_UPD(E, V) update_inst<E, V>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, s)
     switch (cfg.variant * 8 + cfg.ept) {
         case 1: CC_UPD(1, 0); break;
         case 2: CC_UPD(2, 0); break;
@@ -442,9 +494,9 @@ cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevSt
         case 17: CC_UPD(1, 2); break;
         case 18: CC_UPD(2, 2); break;
         case 20: CC_UPD(4, 2); break;
-        case 25: update_deep_inst<1>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, s); break;
-        case 26: update_deep_inst<2>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, s); break;
-        case 28: update_deep_inst<4>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, s); break;
+        case 25: update_deep_inst<1>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, s); break;
+        case 26: update_deep_inst<2>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, s); break;
+        case 28: update_deep_inst<4>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, s); break;
         default: return cudaErrorInvalidValue;
     }
 #undef CC_UPD
@@ -603,6 +655,109 @@ k_query(int* __restrict__ parent, int n, const int* __restrict__ pairs, int64_t 
     if (bad) flag(ds, ST_RANGE);
 }
 
+// Algorithm 1 with the warp as the unit of work. A warp takes chunks of
+// 32 * CH consecutive pairs; each lane keeps S pairs in flight, and every
+// round advances each unfinished walk one step (read-only, as MODE 0: all
+// of a lane's loads of a round are independent). A finished pair writes its
+// answer, and its slot takes the next pair of the chunk at once: a ballot
+// over the finished slots gives each a distinct index, so the lanes whose
+// walks are short keep working while another lane walks a long path, instead
+// of idling until the warp's longest walk ends. A pair whose first parents
+// are equal is answered after its first round.
+template <int S, int CH>
+__global__ void __launch_bounds__(1024)
+k_query_warp(const int* __restrict__ parent, int n, const int* __restrict__ pairs, int64_t k, int vec,
+             uint8_t* __restrict__ out, DevState* __restrict__ ds) {
+    pdl_trigger();
+    pdl_wait();
+    const unsigned full = 0xffffffffu;
+    const int lane = (int)(threadIdx.x & 31u);
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    bool bad = false, corrupt = false;
+    for (int64_t base = warp * 32 * CH; base < k; base += nwarps * 32 * CH) {
+        const int64_t end = base + 32 * CH < k ? base + 32 * CH : k;
+        int64_t next = base;  // warp-uniform: the next pair of the chunk not yet taken
+        int64_t idx[S];
+        int xu[S], pu[S], xv[S], pv[S];
+        bool act[S], eq[S];
+#pragma unroll
+        for (int j = 0; j < S; j++) {
+            act[j] = false;
+            eq[j] = false;
+            idx[j] = 0;
+            xu[j] = pu[j] = xv[j] = pv[j] = 0;
+        }
+        bool take[S];
+#pragma unroll
+        for (int j = 0; j < S; j++) take[j] = true;
+        while (true) {
+            // hand the next pairs of the chunk to the slots that are free
+#pragma unroll
+            for (int j = 0; j < S; j++) {
+                const unsigned want = __ballot_sync(full, take[j]);
+                if (take[j]) {
+                    idx[j] = next + __popc(want & lt);
+                    act[j] = idx[j] < end;
+                    if (act[j]) {
+                        int u, v;
+                        if (vec >= 1) {
+                            const int2 q = __ldcs(reinterpret_cast<const int2*>(pairs) + idx[j]);
+                            u = q.x;
+                            v = q.y;
+                        } else {
+                            u = __ldcs(pairs + 2 * idx[j]);
+                            v = __ldcs(pairs + 2 * idx[j] + 1);
+                        }
+                        if (!(in_range(u, n) && in_range(v, n))) {
+                            bad = true;
+                            out[idx[j]] = 0;
+                            act[j] = false;
+                        } else {
+                            xu[j] = u;
+                            xv[j] = v;
+                            pu[j] = __ldg(parent + u);
+                            pv[j] = __ldg(parent + v);
+                            eq[j] = pu[j] == pv[j];
+                        }
+                    }
+                    take[j] = false;
+                }
+                next += __popc(want);
+            }
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < S; j++) any |= act[j];
+            if (!__any_sync(full, any) && next >= end) break;
+            // one step of every unfinished walk; finished pairs answer and free their slot
+#pragma unroll
+            for (int j = 0; j < S; j++) {
+                if (!act[j]) {
+                    take[j] = next < end;  // an idle slot takes a pair while the chunk has any
+                    continue;
+                }
+                if (!eq[j] && pu[j] < xu[j]) {
+                    xu[j] = pu[j];
+                    pu[j] = __ldg(parent + xu[j]);
+                }
+                if (!eq[j] && pv[j] < xv[j]) {
+                    xv[j] = pv[j];
+                    pv[j] = __ldg(parent + xv[j]);
+                }
+                if (eq[j] || (pu[j] >= xu[j] && pv[j] >= xv[j])) {
+                    if (!eq[j] && (pu[j] > xu[j] || pv[j] > xv[j])) corrupt = true;
+                    out[idx[j]] = (uint8_t)(eq[j] || xu[j] == xv[j]);
+                    act[j] = false;
+                    take[j] = true;
+                }
+            }
+        }
+    }
+    if (bad) flag(ds, ST_RANGE);
+    if (corrupt) flag(ds, ST_CORRUPT);
+}
+
 template <int E, int MODE, bool PERSIST>
 static void query_one(unsigned g, int block, const cudaAccessPolicyWindow* window, int pdl, cudaStream_t s,
                       int* parent, int n, const int* pairs, int64_t k, int vec, uint8_t* out, int ovec,
@@ -631,6 +786,16 @@ static void query_inst(unsigned g, Launch cfg, cudaStream_t s, int* parent, int 
 cudaError_t launch_query(int* parent, int n, const int* pairs, int64_t k, uint8_t* out,
                          DevState* ds, int mode, Launch cfg, cudaStream_t s) {
     if (k <= 0) return cudaSuccess;
+    if (cfg.query_variant == 2) {  // warp-cooperative, read-only walks whatever the mode
+        constexpr int kS = 2, kCH = 16;
+        const int64_t warps = (k + 32 * kCH - 1) / (32 * kCH);
+        int64_t g = (warps * 32 + cfg.block - 1) / cfg.block;
+        const int64_t cap = resident_grid<k_query_warp<kS, kCH>>(cfg.block);
+        if (g > cap) g = cap;
+        launch_windowed(k_query_warp<kS, kCH>, (unsigned)g, cfg.block, s, cfg.window, cfg.pdl != 0, (const int*)parent,
+                        n, pairs, k, pair_vec(pairs), out, ds);
+        return cudaGetLastError();
+    }
     if (cfg.qept) cfg.ept = cfg.qept;
     const int vec = pair_vec(pairs);
     const int ovec = (reinterpret_cast<uintptr_t>(out) % cfg.ept) == 0;

@@ -237,7 +237,10 @@ cudaError_t launch_order_edges(const int* edges, int64_t k, int n, int log_bucke
     int* totals = counters;
     int* fill = counters + nb;
     unsigned* done = reinterpret_cast<unsigned*>(counters + 2 * nb);
-    cudaError_t e = launch_pdl(k_order_count, (unsigned)G, s, pdl != 0, edges, k, vec, n, shift, nb, totals,
+    // The count kernel becomes a dependent launch only when it reads its
+    // edges before the wait (pdl 2): launched early just to wait, its CTAs
+    // would hold SM slots that the previous kernel's remaining CTAs need.
+    cudaError_t e = launch_pdl(k_order_count, (unsigned)G, s, pdl == 2, edges, k, vec, n, shift, nb, totals,
                                (int)(pdl == 2));
     if (e != cudaSuccess) return e;
     e = launch_pdl(k_order_scatter, (unsigned)G, s, pdl != 0, edges, k, vec, n, shift, nb, totals, fill, done,

@@ -42,15 +42,16 @@ PLAIN_SPACE = {
     "compress_scope": [0, 1],
     "query_halving": [0, 1, 2],
     "l2_persist": [0, 1],
-    "query_variant": [0, 1],
+    "query_variant": [0, 1, 2],
     "pdl": [0, 1, 2],
     "query_pairs_per_thread": [0, 1, 2, 4],
     "hook": [0, 1, 2],
     "edge_order": [0, 7, 9],
+    "hook_warp": [0, 1],
 }
 PLAIN_START = {"update_variant": 0, "edges_per_thread": 2, "block": 256, "compress_every": 1,
                "compress_scope": 0, "query_halving": 0, "l2_persist": 0, "query_variant": 0,
-               "pdl": 1, "query_pairs_per_thread": 0, "hook": 0, "edge_order": 0}
+               "pdl": 1, "query_pairs_per_thread": 0, "hook": 0, "edge_order": 0, "hook_warp": 0}
 
 SEG_SPACE = {
     "seg_block": [128, 256, 512, 1024],

@@ -67,6 +67,22 @@ OPTION_SETS = {
     "order9_two_pass": {"edge_order": 9, "update_variant": 4, "edges_per_thread": 2, "pdl": 2,
                          "compress_every": 4},
     "order8_paper_schedule": {"edge_order": 8, "update_schedule": 1},
+    "warp_hook_lockstep": {"hook_warp": 1, "update_variant": 1, "edges_per_thread": 2, "block": 96},
+    "warp_hook_persistent_min": {"hook_warp": 1, "hook": 1, "update_variant": 2, "edges_per_thread": 4,
+                                 "compress_every": 0},
+    "warp_hook_deep_first_min": {"hook_warp": 1, "hook": 2, "update_variant": 3, "edges_per_thread": 2,
+                                 "block": 512, "compress_every": 0, "pdl": 2},
+    "warp_hook_deep_ept1": {"hook_warp": 1, "update_variant": 3, "edges_per_thread": 1, "block": 128,
+                            "compress_every": 2},
+    "warp_hook_two_pass": {"hook_warp": 1, "update_variant": 4, "edges_per_thread": 2, "compress_every": 0},
+    "warp_hook_two_pass_min": {"hook_warp": 1, "hook": 1, "update_variant": 4, "edges_per_thread": 1},
+    "warp_hook_ordered": {"hook_warp": 1, "edge_order": 8, "update_variant": 2, "edges_per_thread": 1,
+                          "block": 128, "compress_every": 4},
+    "warp_hook_per_edge_ignored": {"hook_warp": 1, "update_variant": 0},
+    "warp_query": {"query_variant": 2, "compress_every": 0},
+    "warp_query_flat_b1024": {"query_variant": 2, "compress_every": 1, "block": 1024},
+    "warp_query_halving_ignored_pdl2": {"query_variant": 2, "query_halving": 1, "compress_every": 3, "pdl": 2,
+                                        "block": 64},
 }
 
 
@@ -126,7 +142,10 @@ def test_uniform_small_every_batch(cc, opts):
                                   "persistent_query_halving", "splitting_query", "deep_prefetch_ept2_pdl2",
                                   "two_pass_ept4", "query_ept2_update_ept4", "min_hook", "min_hook_persistent",
                                   "min_hook_deep", "min_hook_two_pass", "min_hook_first_only", "order8",
-                                  "order6", "order7_deep_min_hook", "order8_paper_schedule"])
+                                  "order6", "order7_deep_min_hook", "order8_paper_schedule",
+                                  "warp_hook_lockstep", "warp_hook_persistent_min", "warp_hook_deep_first_min",
+                                  "warp_hook_two_pass", "warp_hook_ordered", "warp_query",
+                                  "warp_query_halving_ignored_pdl2"])
 def test_rmat_small(cc, opts):
     s = I.rmat_stream(scale=16, m=1 << 20, batch=(1 << 16) + 3, q=(1 << 16) - 5, seed=1)
     run_stream(cc, s, OPTION_SETS[opts], label_every=4, check_invariants=True)
@@ -135,7 +154,9 @@ def test_rmat_small(cc, opts):
 @pytest.mark.parametrize("opts", ["default", "no_compress", "ept4_b1024", "compress_every3",
                                   "lockstep", "persistent_ept1_b1024", "splitting_query",
                                   "deep_prefetch_ept1_b1024", "two_pass_ept1_pdl0", "min_hook",
-                                  "min_hook_deep", "order8", "order9_persistent_pdl2", "order9_two_pass"])
+                                  "min_hook_deep", "order8", "order9_persistent_pdl2", "order9_two_pass",
+                                  "warp_hook_deep_ept1", "warp_hook_two_pass_min", "warp_hook_ordered",
+                                  "warp_query", "warp_query_flat_b1024"])
 def test_grid_small(cc, opts):
     s = I.grid_stream(512, 512, batch=(1 << 14) + 1, q=1 << 14, seed=2)
     ref = run_stream(cc, s, OPTION_SETS[opts], label_every=8, check_invariants=True)
@@ -262,7 +283,7 @@ OPTION_RANGES = [
     ("query_halving", [-1, 3], [0, 1, 2]),
     ("profile", [2], [0, 1]),
     ("update_variant", [-1, 5], [0, 1, 2, 3, 4]),
-    ("query_variant", [2], [0, 1]),
+    ("query_variant", [-1, 3], [0, 1, 2]),
     ("pdl", [-1, 3], [0, 1, 2]),
     ("query_pairs_per_thread", [3, 8], [0, 1, 2, 4]),
     ("hook", [-1, 3], [0, 1, 2]),
@@ -270,6 +291,7 @@ OPTION_RANGES = [
     ("update_schedule", [2], [0, 1]),
     ("sv_graph", [-1, 2], [0, 1]),
     ("edge_order", [-1, 1, 5, 10], [0, 6, 9]),
+    ("hook_warp", [-1, 2], [0, 1]),
 ]
 
 

@@ -2,7 +2,8 @@
 
 Every update variant, with compare-and-swap hooks and with the atomicMin hook
 (whose correctness rests on an argument about concurrent displacement and
-repair), runs many small seeded streams of varied shape -- hub-heavy,
+repair), each also with the hooks of a warp grouped by target root, runs
+many small seeded streams of varied shape -- hub-heavy,
 uniform, long descending paths, many duplicate edges -- cut into minibatches
 of random, ragged sizes. After every minibatch the labels (minimum vertex id
 per component) and a batch of query answers must equal the oracle's exactly.
@@ -71,6 +72,14 @@ CONFIGS = {
     "v3_min": {"update_variant": 3, "edges_per_thread": 1, "hook": 1, "compress_every": 0, "block": 1024},
     "v4_min": {"update_variant": 4, "edges_per_thread": 2, "hook": 1, "compress_every": 2},
     "v3_min_first": {"update_variant": 3, "edges_per_thread": 2, "hook": 2, "compress_every": 0, "pdl": 2},
+    # hooks grouped per warp by target root (hook_warp), both link primitives
+    "v1_cas_warp": {"update_variant": 1, "edges_per_thread": 2, "block": 64, "hook_warp": 1},
+    "v2_min_warp": {"update_variant": 2, "edges_per_thread": 1, "hook": 1, "compress_every": 0, "hook_warp": 1},
+    "v3_cas_warp": {"update_variant": 3, "edges_per_thread": 4, "compress_every": 0, "hook_warp": 1},
+    "v3_min_warp": {"update_variant": 3, "edges_per_thread": 2, "hook": 1, "compress_every": 0, "hook_warp": 1,
+                    "pdl": 2},
+    "v4_cas_warp": {"update_variant": 4, "edges_per_thread": 1, "compress_every": 0, "hook_warp": 1},
+    "v4_min_warp": {"update_variant": 4, "edges_per_thread": 4, "hook": 1, "compress_every": 3, "hook_warp": 1},
 }
 
 
