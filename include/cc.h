@@ -90,7 +90,11 @@ typedef enum {
                                     Bulk-Query kernels are launched with an access-policy window
                                     over the forest (a per-launch attribute; the stream is not
                                     changed), and the process's persisting-L2 limit is raised to
-                                    the forest size, capped by the device maximum. Default 0 */
+                                    the forest size, capped by the device maximum. When the last
+                                    handle with the option on leaves a device (set to 0, or
+                                    destroyed), the limit found before is restored and all
+                                    persisting lines are reset to normal
+                                    (cudaCtxResetPersistingL2Cache). Default 0 */
     CC_OPT_SEG_BLOCK = 8,        /* batched form: threads per CTA of the persistent kernel (default 512) */
     CC_OPT_SEG_EDGES_PER_THREAD = 9, /* batched form: edges (pairs) per thread per step: 1, 2, 4 (default 1) */
     CC_OPT_SEG_SMEM_CAP = 10,    /* batched form: graphs of at most this many vertices are processed in

@@ -8,6 +8,7 @@
 #include <new>
 #include <string>
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "cc.h"
@@ -49,6 +50,50 @@ struct DeviceScope {
         if (prev >= 0) cudaSetDevice(prev);
     }
 };
+
+// Persisting-L2 bookkeeping per device (CC_OPT_L2_PERSIST). Handles with an
+// access-policy window raise the context's persisting-L2 limit; when the last
+// of them on a device lets go (option off, or destroyed) the limit found
+// before the first one is put back and every persisting line is turned back
+// into a normal one. Without that, lines of a freed forest stay persisting,
+// and with the raised set-aside they keep that part of L2 from every later
+// kernel in the process.
+struct PersistState {
+    int users = 0;
+    size_t saved_limit = 0;  // the limit before the first user raised it
+    size_t limit = 0;        // the limit as raised
+};
+std::mutex g_persist_mu;
+PersistState g_persist[64];
+
+cudaError_t persist_acquire(int dev, size_t want) {
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_persist_mu);
+    PersistState& p = g_persist[dev];
+    if (p.users == 0) {
+        cudaError_t e = cudaDeviceGetLimit(&p.saved_limit, cudaLimitPersistingL2CacheSize);
+        if (e != cudaSuccess) return e;
+        p.limit = p.saved_limit;
+    }
+    if (want > p.limit) {
+        cudaError_t e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want);
+        if (e != cudaSuccess) return e;
+        p.limit = want;
+    }
+    p.users++;
+    return cudaSuccess;
+}
+
+// Called with the device current and the releasing handle's work finished.
+void persist_release(int dev) {
+    if (dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(g_persist_mu);
+    PersistState& p = g_persist[dev];
+    if (p.users <= 0 || --p.users > 0) return;
+    cudaCtxResetPersistingL2Cache();
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, p.saved_limit);
+    p.limit = p.saved_limit;
+}
 
 const int64_t kDefaults[CC_OPT__COUNT] = {256, 2, 1, CC_COMPRESS_ALL, 0, 0, 0, 0,
                                           512, 1, 65536, 1, 0, 0, 0, 0, 0, 1, 0, 0, 1, 0, 0};
@@ -539,6 +584,7 @@ cc_status cc_destroy(cc_ctx* c) {
         cudaFree(c->order_buf);
         cudaFree(c->order_hist);
         cc::bulk_find_free(c->bf);
+        if (c->window.num_bytes > 0) persist_release(c->device);
         cudaFree(c->parent);
         cudaFree(c->ds);
     }
@@ -1046,9 +1092,19 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
             break;
         case CC_OPT_L2_PERSIST: {
             if (value != 0 && value != 1) return fail(CC_ERR_ARG, "option %d takes 0 or 1", option);
-            c->window = cudaAccessPolicyWindow{};
-            if (value) {
-                DeviceScope scope(c->device);
+            const bool had = c->window.num_bytes > 0;
+            if (value && had) break;  // already on
+            DeviceScope scope(c->device);
+            if (!value) {
+                if (had) {
+                    cudaError_t e = cudaStreamSynchronize(c->stream);
+                    if (e != cudaSuccess) return cuda_fail(e, "L2 persist off: sync");
+                    c->window = cudaAccessPolicyWindow{};
+                    persist_release(c->device);
+                }
+                break;
+            }
+            {
                 int max_persist = 0, max_window = 0;
                 cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, c->device);
                 cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, c->device);
@@ -1056,7 +1112,7 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
                     return fail(CC_ERR_UNSUPPORTED, "no persisting L2 on this device");
                 const size_t bytes = (size_t)c->n * sizeof(int);
                 const size_t limit = bytes < (size_t)max_persist ? bytes : (size_t)max_persist;
-                cudaError_t e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, limit);
+                cudaError_t e = persist_acquire(c->device, limit);
                 if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSetLimit(persisting L2)");
                 c->window.base_ptr = c->parent;
                 c->window.num_bytes = bytes < (size_t)max_window ? bytes : (size_t)max_window;

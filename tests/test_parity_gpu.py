@@ -310,6 +310,54 @@ def test_option_ranges(cc, name, bad, good):
     f.close()
 
 
+def _cudart():
+    import ctypes
+    for name in ("libcudart.so.13", "libcudart.so", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    pytest.skip("no CUDA runtime library to query the limit with")
+
+
+def test_l2_persist_gives_back_the_limit_and_lines(cc):
+    # handles with l2_persist raise the context's persisting-L2 limit (to their
+    # forest size, capped by the device maximum); when the last one leaves
+    # (option off or destroyed) the limit found before is back, so later
+    # kernels of the process get the whole L2 again
+    import ctypes
+    rt = _cudart()
+    PERSISTING_L2 = 6            # cudaLimitPersistingL2CacheSize
+    ATTR_MAX_PERSISTING = 108    # cudaDevAttrMaxPersistingL2CacheSize
+
+    def limit():
+        v = ctypes.c_size_t()
+        assert rt.cudaDeviceGetLimit(ctypes.byref(v), PERSISTING_L2) == 0
+        return v.value
+
+    torch.zeros(1, device="cuda")
+    mx = ctypes.c_int()
+    assert rt.cudaDeviceGetAttribute(ctypes.byref(mx), ATTR_MAX_PERSISTING, torch.cuda.current_device()) == 0
+    before = limit()
+    can_raise = mx.value > before
+    f = cc.Forest(1 << 25, l2_persist=1)         # 128 MiB forest: asks for the device maximum
+    g = cc.Forest(1 << 18, l2_persist=1)
+    raised = limit()
+    assert raised >= before and (raised > before) == can_raise
+    f.bulk_update(dev(I.uniform_pairs(1 << 25, 1 << 16, seed=1, tag=I.TAG_EDGES)))
+    f.sync()
+    f.close()
+    assert limit() == raised                     # g still has its window
+    g.set_option("l2_persist", 1)                # already on: no second claim
+    g.set_option("l2_persist", 0)
+    assert limit() == before
+    h = cc.Forest(1 << 25, l2_persist=1)
+    assert limit() == raised
+    h.close()
+    g.close()
+    assert limit() == before
+
+
 def test_checkpoint_resume(cc):
     s = I.rmat_stream(scale=14, m=1 << 17, batch=1 << 13, q=1 << 12, seed=4)
     whole = cc.Forest(s.n)
