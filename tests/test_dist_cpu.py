@@ -75,3 +75,17 @@ def test_reference_arm_line_has_the_contract_keys():
     assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and cpu["value"] == d["value"] and cpu["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_on_the_headline_workload():
+    """With no --workload the reference arm times the oracle on the headline
+    workload (the 8192 x 8192 grid), one step being a pass over a sample of
+    every minibatch, and reports it on the GPU arm's metric and unit."""
+    sys.path.insert(0, str(ROOT))
+    import bench
+    ns = bench.argparse.Namespace(workload=bench.HEADLINE, steps=1, warmup=3, ref_fraction=256)
+    d = bench.run_reference(ns, 0, 1)
+    assert bench.HEADLINE == "grid"
+    assert d["impl"] == "reference" and d["unit"] == "edges/s" and d["value"] > 0
+    assert "8192x8192" in d["config"]["workload"] and "pass" in d["config"]["step"]
+    assert d["cpu_baseline"]["value"] == d["value"]

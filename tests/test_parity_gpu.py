@@ -452,6 +452,14 @@ def test_full_size_grid_stream(cc):
     assert int(lab.max()) == 0 and f.components() == 1 == ref.components
 
 
+def test_uniform_stream_at_the_benchmarked_options(cc):
+    # n = 2^16, 16 minibatches of 2^16 uniform edges, 2^16 queries after each,
+    # at the options the benchmark's uniform form times: every answer and the
+    # labels after every minibatch
+    from bench import launch_options
+    run_stream(cc, I.uniform_stream(), launch_options("uniform"), label_every=1)
+
+
 def test_paper_scale_random_stream_component_curve(cc):
     # 10^8 vertices, 5x10^8 uniform edges in minibatches of 10^7 (the paper's
     # largest batch, Table 3): component count after every minibatch (the
