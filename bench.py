@@ -776,6 +776,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int, dist, workload: str | 
                 "in_step_share": round(dk["ms_total"] / total_ms, 4),
                 "in_step_share_what": "the dominant kernel's summed event time over the same K "
                                       "passes / the pass time of the value's region"}
+    if roofline["traffic"]:
+        # the measured DRAM bytes of the same kernel over the same launch time
+        roofline["traffic_GBps"] = round(roofline["traffic"] / (dk["us_avg"] * 1e-6) / 1e9, 1)
+        roofline["traffic_frac"] = round(roofline["traffic_GBps"] / peak, 4)
     if gather:
         gather["frac_of_peak"] = round(gather["GBps"] / peak, 4)
         gather["dominant_kernel_frac_of_this"] = round(achieved / gather["GBps"], 4)
