@@ -261,6 +261,31 @@ def test_edge_order_ragged_sizes_and_bad_ids(cc, log_buckets):
     f.sync()
 
 
+@pytest.mark.parametrize("hub", ["first", "last"])
+def test_edge_order_with_every_edge_in_one_bucket(cc, hub):
+    # a star minibatch whose smaller endpoints all fall into one bucket (hub 0:
+    # every edge in bucket 0; hub n-1: the other endpoints spread, then a
+    # second star with every edge inside the last bucket's id range)
+    n = 1 << 20
+    rng = np.random.default_rng(7)
+    f = cc.Forest(n, edge_order=9, update_variant=2, edges_per_thread=1, block=128, hook=1,
+                  compress_every=0)
+    ref = oracle.OracleUF(n)
+    h = 0 if hub == "first" else n - 1
+    others = rng.integers(0, n, size=300000).astype(np.int32)
+    e1 = np.stack([np.full_like(others, h), others], 1)
+    lo = n - (n >> 9)                                      # the last bucket's first id
+    tail = rng.integers(lo, n, size=50000).astype(np.int32)
+    e2 = np.stack([tail, np.roll(tail, 1)], 1)
+    for e in (e1, e2):
+        f.bulk_update(dev(e))
+        ref.bulk_update(e)
+        q = rng.integers(0, n, size=(100000, 2)).astype(np.int32)
+        assert np.array_equal(f.bulk_query(dev(q)).cpu().numpy(), ref.bulk_query(q))
+    assert np.array_equal(f.labels().cpu().numpy(), ref.labels())
+    f.sync()
+
+
 def test_argument_errors_leave_state(cc):
     f = cc.Forest(10)
     with pytest.raises(TypeError):
