@@ -1165,7 +1165,9 @@ def main(argv=None) -> int:
             out = run_paper(args, rank, world, local_rank, dist)
         else:
             sub = {}
-            with_forms = args.workload == HEADLINE and forms
+            # Under torchrun (N > 1) every rank is a replica of the headline
+            # only: the other forms are single-GPU comparisons.
+            with_forms = args.workload == HEADLINE and forms and world == 1
             # The served form goes first: its copies from pinned host memory
             # run fastest before the process has pinned and copied other
             # streams (the plain forms time device-resident inputs).
