@@ -85,7 +85,11 @@ typedef enum {
                                     and lists the edges whose parents differ (16 B each; the list,
                                     room for the largest minibatch so far, is allocated on first
                                     use and grown with one stream synchronisation), then a pass
-                                    that walks and hooks only the listed edges (default 0) */
+                                    that walks and hooks only the listed edges; 5 = a persistent
+                                    grid over tiles: every thread reads its edges' first parents,
+                                    the open edges go to a list in shared memory, and the whole
+                                    CTA walks and hooks that list while the next tile's reads are
+                                    in flight (default 0) */
     CC_OPT_L2_PERSIST = 7,       /* 1: ask L2 to keep the forest resident: the Bulk-Update and
                                     Bulk-Query kernels are launched with an access-policy window
                                     over the forest (a per-launch attribute; the stream is not

@@ -1088,7 +1088,7 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
                 return fail(CC_ERR_ARG, "edge order %lld: need 0 (off) or 6..9 (log2 of the bucket count)", (long long)value);
             break;
         case CC_OPT_UPDATE_VARIANT:
-            if (value < 0 || value > 4) return fail(CC_ERR_ARG, "update variant %lld: need 0..4", (long long)value);
+            if (value < 0 || value > 5) return fail(CC_ERR_ARG, "update variant %lld: need 0..5", (long long)value);
             break;
         case CC_OPT_L2_PERSIST: {
             if (value != 0 && value != 1) return fail(CC_ERR_ARG, "option %d takes 0 or 1", option);

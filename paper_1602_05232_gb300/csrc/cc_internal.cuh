@@ -30,7 +30,8 @@ struct Launch {
     int ept;          // edges (pairs) per thread: 1, 2 or 4
     int variant = 0;  // update kernel: 0 per-edge walks, 1 lockstep walks, 2 persistent + prefetch,
                       // 3 persistent + two-stage prefetch (edges two chunks ahead, parents one),
-                      // 4 filter pass + live-edge pass (launch_update_split)
+                      // 4 filter pass + live-edge pass (launch_update_split),
+                      // 5 persistent tiles whose open edges the whole CTA walks from a shared-memory list
     int query_variant = 0;  // query kernel: 0 one chunk per thread, 1 persistent + prefetch
     const cudaAccessPolicyWindow* window = nullptr;  // L2 window over the forest, or none
     int pdl = 0;  // programmatic dependent launch: 0 off, 1 wait first, 2 first pairs before the wait

@@ -343,6 +343,132 @@ static void update_deep_inst(const int* edges, int64_t k, int vec, int* parent, 
                     ds, (int)(pdl == 2), minhook);
 }
 
+// --- VARIANT 5: per-CTA list of open edges ---------------------------------
+//
+// A persistent grid over tiles of blockDim * E edges. Every thread reads its
+// E edges' first parents (independent loads, as in the filter pass of
+// variant 4); the open edges (parents differ) go to a list in shared memory,
+// and then all threads of the CTA walk and hook that list together, two
+// listed edges per thread at a time, while the edge loads and first parent
+// reads of the CTA's next tile are already in flight. So the walks of the few
+// open edges are spread over every thread of the CTA instead of stalling the
+// warp that happened to load them. Two barriers per tile; the list's counter
+// is double-buffered so that a count is cleared only after every thread has
+// read it.
+template <int E>
+__global__ void __launch_bounds__(1024, 1)  // without the minimum, E = 1 and 2 were held to 32 registers and spilled
+k_update_tiles(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
+               DevState* __restrict__ ds, int early, int minhook) {
+    extern __shared__ int4 open_list[];  // blockDim.x * E entries: (u, v, parent[u], parent[v])
+    __shared__ unsigned n_open[2];
+    pdl_trigger();
+    if (!early) pdl_wait();
+    const int64_t T = (int64_t)blockDim.x * E;
+    const int64_t tiles = (k + T - 1) / T;
+    if (threadIdx.x == 0) n_open[0] = n_open[1] = 0u;
+    int made = 0;
+    int64_t t = blockIdx.x;
+    int u[E] = {}, v[E] = {}, pu[E], pv[E];
+    unsigned m = 0;
+    int64_t e0 = t * T + (int64_t)threadIdx.x * E;
+    if (t < tiles && e0 < k) load_pairs<E>(edges, e0, k, vec, u, v);
+    if (early) pdl_wait();
+    if (t < tiles && e0 < k) m = edge_mask<E>(n, u, v, e0, k, ds);
+    gather_parents<E>(parent, m, u, v, pu, pv);
+    __syncthreads();  // counters cleared
+    const unsigned lane = threadIdx.x & 31u;
+    for (int sel = 0; t < tiles; t += gridDim.x, sel ^= 1) {
+        // append this thread's open edges (one atomic per warp)
+        unsigned open = 0;
+#pragma unroll
+        for (int i = 0; i < E; i++)
+            if (((m >> i) & 1u) && pu[i] != pv[i]) open |= 1u << i;
+        const int mine = __popc(open);
+        int incl = mine;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= (unsigned)d) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned base = 0;
+        if (lane == 31 && total) base = atomicAdd(&n_open[sel], (unsigned)total);
+        base = __shfl_sync(0xffffffffu, base, 31) + (unsigned)(incl - mine);
+#pragma unroll
+        for (int i = 0; i < E; i++)
+            if ((open >> i) & 1u) open_list[base++] = make_int4(u[i], v[i], pu[i], pv[i]);
+        __syncthreads();  // A: the list of this tile is complete
+        const unsigned cnt = n_open[sel];
+        if (threadIdx.x == 0) n_open[sel ^ 1] = 0u;  // last read before the previous B
+        // the next tile's edges and first parents, in flight during the walks
+        const int64_t t1 = t + gridDim.x;
+        const int64_t e1 = t1 * T + (int64_t)threadIdx.x * E;
+        int nu[E] = {}, nv[E] = {};
+        unsigned m1 = 0;
+        if (t1 < tiles && e1 < k) {
+            load_pairs<E>(edges, e1, k, vec, nu, nv);
+            m1 = edge_mask<E>(n, nu, nv, e1, k, ds);
+        }
+        int npu[E], npv[E];
+        gather_parents<E>(parent, m1, nu, nv, npu, npv);
+        // walk and hook the list, two entries per thread at a time
+        for (unsigned j = 2u * threadIdx.x; j < cnt; j += 2u * blockDim.x) {
+            const int4 a = open_list[j];
+            const int4 b = j + 1 < cnt ? open_list[j + 1] : a;
+            const unsigned on = j + 1 < cnt ? 3u : 1u;
+            const int lu[2] = {a.x, b.x}, lv[2] = {a.y, b.y}, lpu[2] = {a.z, b.z}, lpv[2] = {a.w, b.w};
+            made += walk_and_hook<2>(parent, on, lu, lv, lpu, lpv, ds, minhook);
+        }
+        __syncthreads();  // B: the list has been walked; it may be refilled
+#pragma unroll
+        for (int i = 0; i < E; i++) {
+            u[i] = nu[i]; v[i] = nv[i]; pu[i] = npu[i]; pv[i] = npv[i];
+        }
+        m = m1;
+    }
+    made = __reduce_add_sync(0xffffffffu, made);
+    if ((threadIdx.x & 31) == 0 && made) atomicAdd(&ds->unions, (unsigned long long)made);
+}
+
+template <int E>
+static void update_tiles_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds, int block,
+                              const cudaAccessPolicyWindow* window, int pdl, int minhook, cudaStream_t s) {
+    const size_t smem = sizeof(int4) * (size_t)block * E;
+    if (smem > 48 * 1024)  // the largest list (1024 threads x 4 edges) needs 64 KiB
+        cudaFuncSetAttribute(k_update_tiles<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_tiles<E>, block, smem);
+    int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
+    const int64_t cap = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    if (g > cap) g = cap;
+    if (!window && !pdl) {
+        k_update_tiles<E><<<(unsigned)g, block, smem, s>>>(parent, n, edges, k, vec, ds, 0, minhook);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)g);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    unsigned na = 0;
+    if (window) {
+        attr[na].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[na].val.accessPolicyWindow = *window;
+        na++;
+    }
+    if (pdl) {
+        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na].val.programmaticStreamSerializationAllowed = 1;
+        na++;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    cudaLaunchKernelEx(&cfg, k_update_tiles<E>, parent, n, edges, k, vec, ds, (int)(pdl == 2), minhook);
+}
+
 // --- VARIANT 4: filter pass + live-edge pass ------------------------------
 //
 // Once the forest is shallow, almost every edge of a minibatch already has
@@ -497,6 +623,9 @@ cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevSt
         case 25: update_deep_inst<1>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, s); break;
         case 26: update_deep_inst<2>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, s); break;
         case 28: update_deep_inst<4>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, s); break;
+        case 41: update_tiles_inst<1>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, s); break;
+        case 42: update_tiles_inst<2>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, s); break;
+        case 44: update_tiles_inst<4>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, s); break;
         default: return cudaErrorInvalidValue;
     }
 #undef CC_UPD

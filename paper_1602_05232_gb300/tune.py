@@ -35,7 +35,7 @@ from . import inputs as I
 CACHE = Path(__file__).resolve().parent / "tuned.json"
 
 PLAIN_SPACE = {
-    "update_variant": [0, 1, 2, 3, 4],
+    "update_variant": [0, 1, 2, 3, 4, 5],
     "edges_per_thread": [1, 2, 4],
     "block": [128, 256, 512, 1024],
     "compress_every": [0, 1, 2, 4, 8, 16],

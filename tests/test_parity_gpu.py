@@ -79,6 +79,11 @@ OPTION_SETS = {
     "warp_hook_ordered": {"hook_warp": 1, "edge_order": 8, "update_variant": 2, "edges_per_thread": 1,
                           "block": 128, "compress_every": 4},
     "warp_hook_per_edge_ignored": {"hook_warp": 1, "update_variant": 0},
+    "cta_list_ept1_b128": {"update_variant": 5, "edges_per_thread": 1, "block": 128, "compress_every": 0},
+    "cta_list_ept2_min": {"update_variant": 5, "edges_per_thread": 2, "hook": 1, "pdl": 2, "compress_every": 2},
+    "cta_list_ept4_b1024": {"update_variant": 5, "edges_per_thread": 4, "block": 1024, "hook": 2,
+                            "compress_every": 0},
+    "cta_list_ordered": {"update_variant": 5, "edges_per_thread": 2, "edge_order": 9, "compress_every": 4},
     "warp_query": {"query_variant": 2, "compress_every": 0},
     "warp_query_flat_b1024": {"query_variant": 2, "compress_every": 1, "block": 1024},
     "warp_query_halving_ignored_pdl2": {"query_variant": 2, "query_halving": 1, "compress_every": 3, "pdl": 2,
@@ -144,7 +149,8 @@ def test_uniform_small_every_batch(cc, opts):
                                   "min_hook_deep", "min_hook_two_pass", "min_hook_first_only", "order8",
                                   "order6", "order7_deep_min_hook", "order8_paper_schedule",
                                   "warp_hook_lockstep", "warp_hook_persistent_min", "warp_hook_deep_first_min",
-                                  "warp_hook_two_pass", "warp_hook_ordered", "warp_query",
+                                  "warp_hook_two_pass", "warp_hook_ordered", "warp_query", "cta_list_ept1_b128",
+                                  "cta_list_ept2_min", "cta_list_ept4_b1024",
                                   "warp_query_halving_ignored_pdl2"])
 def test_rmat_small(cc, opts):
     s = I.rmat_stream(scale=16, m=1 << 20, batch=(1 << 16) + 3, q=(1 << 16) - 5, seed=1)
@@ -156,7 +162,7 @@ def test_rmat_small(cc, opts):
                                   "deep_prefetch_ept1_b1024", "two_pass_ept1_pdl0", "min_hook",
                                   "min_hook_deep", "order8", "order9_persistent_pdl2", "order9_two_pass",
                                   "warp_hook_deep_ept1", "warp_hook_two_pass_min", "warp_hook_ordered",
-                                  "warp_query", "warp_query_flat_b1024"])
+                                  "warp_query", "warp_query_flat_b1024", "cta_list_ept1_b128", "cta_list_ordered"])
 def test_grid_small(cc, opts):
     s = I.grid_stream(512, 512, batch=(1 << 14) + 1, q=1 << 14, seed=2)
     ref = run_stream(cc, s, OPTION_SETS[opts], label_every=8, check_invariants=True)
@@ -307,7 +313,7 @@ OPTION_RANGES = [
     ("compress_scope", [2, -1], [0, 1]),
     ("query_halving", [-1, 3], [0, 1, 2]),
     ("profile", [2], [0, 1]),
-    ("update_variant", [-1, 5], [0, 1, 2, 3, 4]),
+    ("update_variant", [-1, 6], [0, 1, 2, 3, 4, 5]),
     ("query_variant", [-1, 3], [0, 1, 2]),
     ("pdl", [-1, 3], [0, 1, 2]),
     ("query_pairs_per_thread", [3, 8], [0, 1, 2, 4]),

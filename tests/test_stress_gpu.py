@@ -72,6 +72,8 @@ CONFIGS = {
     "v3_min": {"update_variant": 3, "edges_per_thread": 1, "hook": 1, "compress_every": 0, "block": 1024},
     "v4_min": {"update_variant": 4, "edges_per_thread": 2, "hook": 1, "compress_every": 2},
     "v3_min_first": {"update_variant": 3, "edges_per_thread": 2, "hook": 2, "compress_every": 0, "pdl": 2},
+    "v5_cas": {"update_variant": 5, "edges_per_thread": 2, "block": 64, "compress_every": 0},
+    "v5_min": {"update_variant": 5, "edges_per_thread": 4, "hook": 1, "compress_every": 0},
     # hooks grouped per warp by target root (hook_warp), both link primitives
     "v1_cas_warp": {"update_variant": 1, "edges_per_thread": 2, "block": 64, "hook_warp": 1},
     "v2_min_warp": {"update_variant": 2, "edges_per_thread": 1, "hook": 1, "compress_every": 0, "hook_warp": 1},
