@@ -161,11 +161,12 @@ __device__ __forceinline__ int update_edges(int* __restrict__ parent, int n,
                 a[i] = x[2 * i];
                 b[i] = x[2 * i + 1];
             }
-            return hook_warp<E>(parent, live, a, b, ds, minhook);
-        }
+            made = hook_warp<E>(parent, live, a, b, ds, minhook);
+        } else {
 #pragma unroll
-        for (int i = 0; i < E; i++)
-            if (live[i]) made += hook_as(parent, x[2 * i], x[2 * i + 1], ds, minhook);
+            for (int i = 0; i < E; i++)
+                if (live[i]) made += hook_as(parent, x[2 * i], x[2 * i + 1], ds, minhook);
+        }
         return made;
     }
 }
@@ -269,6 +270,7 @@ __device__ __forceinline__ int walk_and_hook(int* parent, unsigned m, const int 
         p[2 * i + 1] = live[i] ? pv[i] : v[i];
     }
     walk_split<2 * E>(parent, x, p, ds);
+    int made = 0;
     if constexpr (WARP) {  // every lane of the warp is here (see the kernels)
         int a[E], b[E];
 #pragma unroll
@@ -276,12 +278,12 @@ __device__ __forceinline__ int walk_and_hook(int* parent, unsigned m, const int 
             a[i] = x[2 * i];
             b[i] = x[2 * i + 1];
         }
-        return hook_warp<E>(parent, live, a, b, ds, minhook);
-    }
-    int made = 0;
+        made = hook_warp<E>(parent, live, a, b, ds, minhook);
+    } else {
 #pragma unroll
-    for (int i = 0; i < E; i++)
-        if (live[i]) made += hook_as(parent, x[2 * i], x[2 * i + 1], ds, minhook);
+        for (int i = 0; i < E; i++)
+            if (live[i]) made += hook_as(parent, x[2 * i], x[2 * i + 1], ds, minhook);
+    }
     return made;
 }
 
