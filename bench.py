@@ -224,8 +224,11 @@ def hbm_peak() -> tuple[float, str]:
 
 
 def ncu_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
+    """(DRAM bytes per launch, what was captured) of `kernel` from the committed
+    ncu summary, if it was taken on the current kernel source with the tuned
+    options this run uses (no --opt overrides); else (None, None)."""
+    if OPTION_OVERRIDES:
+        return None, None
     p = ROOT / "profiles" / "ncu_traffic.json"
     try:
         d = json.loads(p.read_text())
@@ -234,9 +237,11 @@ def ncu_traffic(kernel: str, workload: str):
         csrc = ROOT / "paper_1602_05232_gb300" / "csrc"
         files = [csrc / "cc_device.cuh", csrc / "cc_kernels.cu", csrc / "cc_internal.cuh"]
         h = hashlib.sha256(b"".join(f.read_bytes() for f in files)).hexdigest()[:16]
-        return ent["bytes_per_launch"] if ent.get("source_hash") == h else None
+        if ent.get("source_hash") != h:
+            return None, None
+        return ent["bytes_per_launch"], ent.get("kernel")
     except Exception:
-        return None
+        return None, None
 
 
 # ------------------------------------------------------ batched form (segmented)
@@ -780,12 +785,14 @@ def run_gpu(args, rank: int, world: int, local_rank: int, dist, workload: str | 
                 "peak_source": f"of {peak_kind}",
                 "bytes_per_unit": BYTES_PER_UNIT[dom],
                 "units_per_launch": per_launch_units,
-                "traffic": ncu_traffic(dom, workload),
+                "traffic": None,
                 "timing_basis": "per-kernel events, PDL serialised",
                 "in_step_share": round(dk["ms_total"] / total_ms, 4),
                 "in_step_share_what": "the dominant kernel's summed event time over the same K "
                                       "passes / the pass time of the value's region"}
+    roofline["traffic"], traffic_kernel = ncu_traffic(dom, workload)
     if roofline["traffic"]:
+        roofline["traffic_kernel"] = traffic_kernel
         # the measured DRAM bytes of the same kernel over the same launch time
         roofline["traffic_GBps"] = round(roofline["traffic"] / (dk["us_avg"] * 1e-6) / 1e9, 1)
         roofline["traffic_frac"] = round(roofline["traffic_GBps"] / peak, 4)
