@@ -44,10 +44,15 @@ METRIC = ("Bulk-Update edges/s & Bulk-Query queries/s (1 GB300), % HBM roofline;
 
 # Sector-model algorithmic bytes per unit (random 4-byte parent reads cost a
 # 32-byte sector): update 8 B edge + 2 x 32 B; query 8 B pair + 1 B answer +
-# 2 x 32 B; full compression 4 B read + 4 B write per vertex.
+# 2 x 32 B; full compression 4 B read + 4 B write per vertex. With the
+# largest-component filter an edge or pair whose endpoints are both marked
+# reads two 32-byte bitmap sectors in place of two parent sectors (the same
+# bytes in this model; the 1-bit-per-vertex bitmap stays in L2), and a full
+# compression also writes the bitmap, 1/8 B per vertex (BITMAP_BYTES).
 BYTES_PER_UNIT = {"update": 72.0, "query": 73.0, "compress_all": 8.0,
                   "compress_touched": 72.0, "labels": 12.0, "reset": 4.0,
                   "order": 24.0}  # edge order: the edges read twice and written once
+BITMAP_BYTES = 0.125
 
 # Options of the launches this benchmark times, per workload (also used by
 # the full-size parity tests, so they check exactly this configuration).
@@ -766,11 +771,14 @@ def run_gpu(args, rank: int, world: int, local_rank: int, dist, workload: str | 
              "compress_touched": K * s.m,
              "reset": s.n * (launches1["reset"] - launches0["reset"]),
              "order": K * s.m}
+    bpu = dict(BYTES_PER_UNIT)
+    if opts.get("big_filter", 0) and opts.get("compress_every", 1) and not opts.get("compress_scope", 0):
+        bpu["compress_all"] += BITMAP_BYTES
     kernels = {}
     for k, (_, ms) in kstats.items():
         cnt = launches1[k] - launches0[k]
         if cnt and ms > 0:
-            gb = BYTES_PER_UNIT.get(k, 0.0) * units.get(k, 0) / 1e9
+            gb = bpu.get(k, 0.0) * units.get(k, 0) / 1e9
             kernels[k] = {"launches": cnt, "ms_total": round(ms, 4), "us_avg": round(1e3 * ms / cnt, 3),
                           "share": None, "GBps_algorithmic": round(gb / (ms / 1e3), 1) if gb else None}
     tot_k = sum(v["ms_total"] for v in kernels.values()) or 1.0
@@ -779,17 +787,21 @@ def run_gpu(args, rank: int, world: int, local_rank: int, dist, workload: str | 
     dom = max((k for k in kernels if k in units), key=lambda k: kernels[k]["ms_total"])
     dk = kernels[dom]
     per_launch_units = units[dom] / dk["launches"]
-    achieved = BYTES_PER_UNIT[dom] * per_launch_units / (dk["us_avg"] * 1e-6) / 1e9
+    achieved = bpu[dom] * per_launch_units / (dk["us_avg"] * 1e-6) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "peak_source": f"of {peak_kind}",
-                "bytes_per_unit": BYTES_PER_UNIT[dom],
+                "bytes_per_unit": bpu[dom],
                 "units_per_launch": per_launch_units,
                 "traffic": None,
                 "timing_basis": "per-kernel events, PDL serialised",
                 "in_step_share": round(dk["ms_total"] / total_ms, 4),
                 "in_step_share_what": "the dominant kernel's summed event time over the same K "
                                       "passes / the pass time of the value's region"}
+    if opts.get("big_filter", 0) and dom in ("update", "query"):
+        roofline["filter"] = ("largest-component bitmap on: an edge or pair with both endpoints marked "
+                              "reads two L2-resident bitmap sectors in place of two parent sectors "
+                              "(the same sector-model bytes)")
     roofline["traffic"], traffic_kernel = ncu_traffic(dom, workload)
     if roofline["traffic"]:
         roofline["traffic_kernel"] = traffic_kernel
@@ -858,6 +870,8 @@ def gather_ceiling(f, views, reps: int = 20) -> dict | None:
     regions, and run after them (it changes the forest)."""
     if f.kernel_stats().get("query") is None:
         return None
+    big = f.get_option("big_filter")
+    f.set_option("big_filter", 0)               # every pair reads the forest
     f.compress()                                # flat forest: parent equality decides
     bulk_find = f.get_option("bulk_find")
     f.set_option("bulk_find", 0)                # the plain query launch shape, whatever the options
@@ -874,6 +888,7 @@ def gather_ceiling(f, views, reps: int = 20) -> dict | None:
     launches, ms = f.kernel_stats(timing=True)["query"]
     f.set_option("profile", 0)
     f.set_option("bulk_find", bulk_find)
+    f.set_option("big_filter", big)
     launches -= n0
     if launches <= 0 or ms <= 0:
         return None

@@ -172,7 +172,23 @@ typedef enum {
                                     winner's, so a root that many edges of a minibatch hook onto
                                     sees one atomic per warp instead of one per edge. 0 = every
                                     lane hooks on its own (default). Same answers and labels */
-    CC_OPT__COUNT = 23
+    CC_OPT_BIG_FILTER = 23,      /* largest-component filter (the large-component skip of Afforest,
+                                    Sutton, Ben-Nun and Barak, IPDPS 2018). 0 = off (default).
+                                    s in 1..1024 = before every full compression pass (automatic,
+                                    CC_OPT_COMPRESS_EVERY, or cc_compress with CC_COMPRESS_ALL) one
+                                    CTA walks 1024 sampled vertices to their roots; if at least s of
+                                    them reach one root R, that pass also writes a bitmap of n bits
+                                    (bit v = v is in R's tree; 4 bytes per 32 vertices, allocated
+                                    when the option is first set), else the filter stays off until
+                                    the next pass. Trees only merge, so two vertices marked then
+                                    stay connected: the fused Bulk-Query (CC_OPT_QUERY_VARIANT 0, 1)
+                                    answers a pair of marked vertices with 1 without reading the
+                                    forest, and the fused Bulk-Update drops an edge between marked
+                                    vertices before its parent reads. cc_reset, cc_load_labels and
+                                    cc_load_forest turn it off until the next pass. Plain handles,
+                                    default link rule; CC_ERR_UNSUPPORTED on a segmented handle.
+                                    Same answers and labels. Pick launches count as CC_K_BIG_PICK */
+    CC_OPT__COUNT = 24
 } cc_option;
 
 /* Kernel kinds reported by the launch counters and the profiler. */
@@ -186,7 +202,8 @@ typedef enum {
     CC_K_LOAD = 6,
     CC_K_SEGMENTED = 7,
     CC_K_ORDER = 8,          /* the locality order of CC_OPT_EDGE_ORDER (count, scan, scatter) */
-    CC_K__COUNT = 9
+    CC_K_BIG_PICK = 9,       /* the root pick of CC_OPT_BIG_FILTER (one CTA, before a compression) */
+    CC_K__COUNT = 10
 } cc_kernel_kind;
 
 /* ------------------------------------------------------------ lifetime */
@@ -478,6 +495,13 @@ cc_status cc_load_forest(cc_ctx* ctx, const int32_t* parent);
  * to its root, *mean_depth (host, may be NULL) = the mean over all vertices.
  * A diagnostic for the link rules (CC_OPT_LINK). Synchronises. */
 cc_status cc_forest_depth(cc_ctx* ctx, int32_t* max_depth, double* mean_depth);
+
+/* CC_OPT_BIG_FILTER: *root (host) = the root whose tree the bitmap marks, or
+ * -1 while the filter is off; *members (host) = the vertices the last
+ * compression pass marked (0 when *root is -1), counted by a kernel over the
+ * bitmap at this call. A diagnostic. Synchronises.
+ * Errors: CC_ERR_ARG (a NULL output), CC_ERR_CUDA. */
+cc_status cc_big_filter_stats(cc_ctx* ctx, int32_t* root, int64_t* members);
 
 /* *ok = 1 if kernels on the current device can read `p` directly: device or
  * managed memory, or host memory that is pinned and mapped into the device's

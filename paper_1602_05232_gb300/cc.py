@@ -29,13 +29,13 @@ OPTIONS = {"block": OPT_BLOCK, "edges_per_thread": OPT_EDGES_PER_THREAD,
            "seg_max_ctas": 12, "update_schedule": 13, "link": 14,
            "bulk_find": 15, "query_variant": 16, "pdl": 17,
            "query_pairs_per_thread": 18, "hook": 19, "sv_graph": 20, "edge_order": 21,
-           "hook_warp": 22}
+           "hook_warp": 22, "big_filter": 23}
 OP_UPDATE, OP_QUERY = 0, 1
 # Layout of cc_op (include/cc.h): graph, kind, data pointer, k, out pointer.
 OP_DTYPE = np.dtype([("graph", "<i4"), ("kind", "<i4"), ("data", "<u8"), ("k", "<i8"),
                      ("out", "<u8")])
 KERNELS = ["update", "compress_all", "compress_touched", "query", "labels", "reset", "load",
-           "segmented", "order"]
+           "segmented", "order", "big_pick"]
 
 _lib: ctypes.CDLL | None = None
 
@@ -97,6 +97,7 @@ def load(path: str | Path | None = None) -> ctypes.CDLL:
         "cc_bulk_find_stats": [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                                ctypes.POINTER(ctypes.c_int32)],
         "cc_load_forest": [vp, vp],
+        "cc_big_filter_stats": [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -271,6 +272,13 @@ class Forest:
         if parent.dtype != torch.int32 or not parent.is_contiguous() or parent.numel() != self.n:
             raise TypeError("parent: expected a contiguous int32 tensor of n elements")
         check(self._L.cc_load_forest(self._h, parent.data_ptr()), self._L)
+
+    def big_filter_stats(self) -> tuple[int, int]:
+        """(root R whose tree the largest-component bitmap marks or -1 when the
+        filter is off, vertices marked by the last compression pass)."""
+        r, m = ctypes.c_int32(), ctypes.c_int64()
+        check(self._L.cc_big_filter_stats(self._h, ctypes.byref(r), ctypes.byref(m)), self._L)
+        return r.value, m.value
 
     def depth(self) -> tuple[int, float]:
         """(max, mean) distance from a vertex to its root."""

@@ -96,7 +96,7 @@ void persist_release(int dev) {
 }
 
 const int64_t kDefaults[CC_OPT__COUNT] = {256, 2, 1, CC_COMPRESS_ALL, 0, 0, 0, 0,
-                                          512, 1, 65536, 1, 0, 0, 0, 0, 0, 1, 0, 0, 1, 0, 0};
+                                          512, 1, 65536, 1, 0, 0, 0, 0, 0, 1, 0, 0, 1, 0, 0, 0};
 
 // Minibatches below this many edges are never reordered (CC_OPT_EDGE_ORDER):
 // their parent reads are too few to share L2 lines.
@@ -160,6 +160,9 @@ struct cc_ctx {
     int64_t order_hist_cap = 0;     // in ints
     bool order_dirty = false;       // a failed launch may have left the counters non-zero
 
+    // largest-component filter (CC_OPT_BIG_FILTER)
+    unsigned* big = nullptr;        // n bits, written by full compression passes
+
     // union by size (CC_OPT_LINK = 1)
     int* size = nullptr;                 // tree sizes, meaningful at roots
     unsigned long long* best = nullptr;  // per-component vote of the join step
@@ -207,7 +210,13 @@ cc::Launch cfg_of(const cc_ctx* c) {
                       (int)c->opt[CC_OPT_UPDATE_VARIANT], (int)c->opt[CC_OPT_QUERY_VARIANT],
                       c->window.num_bytes > 0 ? &c->window : nullptr, (int)c->opt[CC_OPT_PDL],
                       (int)c->opt[CC_OPT_QUERY_PAIRS_PER_THREAD], (int)(c->opt[CC_OPT_HOOK] == 1),
-                      (int)c->opt[CC_OPT_HOOK_WARP]};
+                      (int)c->opt[CC_OPT_HOOK_WARP], c->opt[CC_OPT_BIG_FILTER] > 0 ? c->big : nullptr};
+}
+
+// The largest-component bitmap no longer describes the forest (reset, or a
+// forest loaded from outside): off until the next full compression pass.
+cudaError_t big_invalidate(cc_ctx* c) {
+    return cudaMemsetAsync(&c->ds->big_root, 0xff, sizeof(int), c->stream);
 }
 
 cc_status check_pairs(const int32_t* p, int64_t k, const char* name) {
@@ -227,8 +236,15 @@ cc_status do_compress(cc_ctx* c, int scope, const int32_t* edges, int64_t k) {
         return s;
     }
     if (scope == CC_COMPRESS_ALL) {
+        unsigned* big = c->opt[CC_OPT_BIG_FILTER] > 0 ? c->big : nullptr;
+        if (big) {
+            cc_status s = run(c, CC_K_BIG_PICK, "compress(all): largest-tree pick", [&] {
+                return cc::launch_big_pick(c->parent, c->n, (int)c->opt[CC_OPT_BIG_FILTER], c->ds, c->stream);
+            });
+            if (s != CC_OK) return s;
+        }
         cc_status s = run(c, CC_K_COMPRESS_ALL, "compress(all)", [&] {
-            return cc::launch_compress_all(c->parent, c->n, nullptr, c->ds, (int)c->opt[CC_OPT_BLOCK], c->stream);
+            return cc::launch_compress_all(c->parent, c->n, nullptr, c->ds, (int)c->opt[CC_OPT_BLOCK], c->stream, big);
         });
         if (s == CC_OK) c->flat = true;
         return s;
@@ -542,6 +558,7 @@ cc_status cc_create(int64_t n, cc_ctx** out) {
                     "cc_create(%lld): %s", (long long)n, cudaGetErrorString(e));
     }
     e = cudaMemsetAsync(c->ds, 0, sizeof(cc::DevState), c->stream);
+    if (e == cudaSuccess) e = big_invalidate(c);
     if (e == cudaSuccess) e = cc::launch_reset(c->parent, n, 256, c->stream);
     c->launches[CC_K_RESET]++;
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -583,6 +600,7 @@ cc_status cc_destroy(cc_ctx* c) {
         cudaFree(c->live_count);
         cudaFree(c->order_buf);
         cudaFree(c->order_hist);
+        cudaFree(c->big);
         cc::bulk_find_free(c->bf);
         if (c->window.num_bytes > 0) persist_release(c->device);
         cudaFree(c->parent);
@@ -619,6 +637,7 @@ cc_status cc_reset(cc_ctx* c) {
     CC_CHECK_CTX(c);
     CC_DEVICE(c);
     cudaError_t e = cudaMemsetAsync(&c->ds->unions, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = big_invalidate(c);
     if (e != cudaSuccess) return cuda_fail(e, "cc_reset");
     cc_status s = run(c, CC_K_RESET, "reset", [&] {
         return cc::launch_reset(c->parent, c->n, (int)c->opt[CC_OPT_BLOCK], c->stream);
@@ -762,6 +781,7 @@ cc_status cc_load_labels(cc_ctx* c, const int32_t* labels) {
     unsigned long long unions = (unsigned long long)c->n - h.roots;
     e = cudaMemcpyAsync(c->parent, labels, (size_t)c->n * sizeof(int), cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&c->ds->unions, &unions, sizeof unions, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = big_invalidate(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cc_load_labels: copy");
     c->flat = true;
@@ -1083,6 +1103,21 @@ cc_status cc_set_option(cc_ctx* c, int32_t option, int64_t value) {
         case CC_OPT_HOOK_WARP:
             if (value != 0 && value != 1) return fail(CC_ERR_ARG, "option %d takes 0 or 1", option);
             break;
+        case CC_OPT_BIG_FILTER:
+            if (value < 0 || value > cc::kBigSample)
+                return fail(CC_ERR_ARG, "big filter %lld: need 0 (off) or 1..%d (least sampled share)", (long long)value, cc::kBigSample);
+            if (value > 0 && c->G > 1) return fail(CC_ERR_UNSUPPORTED, "the largest-component filter on a segmented handle");
+            if (value > 0 && !c->big) {
+                DeviceScope scope(c->device);
+                const size_t words = (size_t)((c->n + 31) / 32);
+                cudaError_t e = cudaMalloc(&c->big, words * sizeof(unsigned));
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    c->big = nullptr;
+                    return fail(CC_ERR_OOM, "big filter: bitmap of %zu words", words);
+                }
+            }
+            break;
         case CC_OPT_EDGE_ORDER:
             if (value != 0 && (value < 6 || value > 9))
                 return fail(CC_ERR_ARG, "edge order %lld: need 0 (off) or 6..9 (log2 of the bucket count)", (long long)value);
@@ -1229,6 +1264,7 @@ cc_status cc_load_forest(cc_ctx* c, const int32_t* parent) {
     unsigned long long unions = (unsigned long long)c->n - h.roots;
     e = cudaMemcpyAsync(c->parent, parent, sizeof(int) * (size_t)c->n, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&c->ds->unions, &unions, sizeof unions, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = big_invalidate(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cc_load_forest: copy");
     c->flat = false;
@@ -1250,6 +1286,25 @@ cc_status cc_forest_depth(cc_ctx* c, int32_t* max_depth, double* mean_depth) {
     if (e != cudaSuccess) return cuda_fail(e, "cc_forest_depth");
     *max_depth = (int32_t)h.max_depth;
     if (mean_depth) *mean_depth = (double)h.sum_depth / (double)c->n;
+    return CC_OK;
+}
+
+cc_status cc_big_filter_stats(cc_ctx* c, int32_t* root, int64_t* members) {
+    CC_CHECK_CTX(c);
+    if (!root || !members) return fail(CC_ERR_ARG, "cc_big_filter_stats: null output");
+    CC_DEVICE(c);
+    cc::DevState h;
+    cudaError_t e = cudaMemcpyAsync(&h, c->ds, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && h.big_root >= 0 && c->big) {  // count the marks
+        e = cudaMemsetAsync(&c->ds->big_members, 0, sizeof(unsigned long long), c->stream);
+        if (e == cudaSuccess) e = cc::launch_big_count(c->big, (c->n + 31) / 32, c->ds, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, c->ds, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cc_big_filter_stats");
+    *root = h.big_root;
+    *members = h.big_root >= 0 ? (int64_t)h.big_members : 0;
     return CC_OK;
 }
 

@@ -219,6 +219,25 @@ __device__ __forceinline__ void walk_split(int* parent, int (&x)[W], int (&p)[W]
     }
 }
 
+// Largest-component filter (the large-component skip of Afforest: Sutton,
+// Ben-Nun and Barak, IPDPS 2018). Bit x of `big` says that x was in the tree
+// of one root R when the bitmap was last written (a full compression pass).
+// Trees only ever merge, so two vertices whose bits are set stay connected
+// whatever is linked afterwards: a query on them answers 1 and an edge
+// between them joins nothing, without a read of the forest. The bitmap is
+// n bits (8 MiB for 2^26 vertices), so it stays in L2 while the forest
+// lines come and go.
+__device__ __forceinline__ bool big_member(const unsigned* __restrict__ big, int x) {
+    return (__ldg(big + (x >> 5)) >> (x & 31)) & 1u;
+}
+
+// The bitmap a kernel may use: `big` when the handle has one and it marks a
+// tree (big_root >= 0), else none. Read after the kernel's wait for the one
+// before it (the compression pass that wrote the bitmap).
+__device__ __forceinline__ const unsigned* big_active(const unsigned* big, const DevState* ds) {
+    return (big && ds->big_root >= 0) ? big : nullptr;
+}
+
 // Read-only walk to the root from x with p = parent[x] already read.
 __device__ __forceinline__ int walk_root(const int* parent, int x, int p) {
     while (p < x) {

@@ -23,6 +23,10 @@ struct DevState {
     unsigned queue;             // work-queue counter of the batched form
     unsigned max_depth;         // forest height diagnostic
     unsigned long long sum_depth;
+    int big_root;               // largest-component filter: the root R whose tree the bitmap
+                                // marks, or -1 = no filter (set by the pick kernel)
+    unsigned big_pad;
+    unsigned long long big_members;  // set bits of the bitmap (launch_big_count, on demand)
 };
 
 struct Launch {
@@ -38,6 +42,8 @@ struct Launch {
     int qept = 0; // pairs per thread of the query kernel (0 = ept)
     int minhook = 0;  // 1: Bulk-Update hooks with atomicMin + repair (hook_min) instead of CAS
     int warphook = 0; // 1: the hooks of a warp are grouped by target root (hook_warp); lockstep variants
+    const unsigned* big = nullptr;  // largest-component bitmap (n bits), or none: pairs whose two
+                                    // endpoints are marked are answered / dropped without walks
 };
 
 // Alignment class of a pair array: 2 = 16-byte, 1 = 8-byte, 0 = 4-byte.
@@ -69,9 +75,19 @@ cudaError_t launch_update_split(int* parent, int n, const int* edges, int64_t k,
 cudaError_t launch_query(int* parent, int n, const int* pairs, int64_t k, uint8_t* out,
                          DevState* ds, int mode, Launch cfg, cudaStream_t s);
 
-// Full compression; also writes labels to `out` when it is not null.
+// Full compression; also writes labels to `out` when it is not null. With
+// `big` (n bits, rounded up to whole 32-bit words), bit v is set to whether v's
+// root is ds->big_root (nothing is written while that is -1).
 cudaError_t launch_compress_all(int* parent, int64_t n, int* out, DevState* ds, int block,
-                                cudaStream_t s);
+                                cudaStream_t s, unsigned* big = nullptr);
+
+// The root of the largest tree, estimated from kBigSample vertices (read-only
+// walks): ds->big_root = that root if at least min_share of the sample reached
+// it, else -1. One CTA.
+constexpr int kBigSample = 1024;
+cudaError_t launch_big_pick(const int* parent, int64_t n, int min_share, DevState* ds, cudaStream_t s);
+// ds->big_members += the set bits of words[0, nwords).
+cudaError_t launch_big_count(const unsigned* words, int64_t nwords, DevState* ds, cudaStream_t s);
 
 cudaError_t launch_compress_touched(int* parent, int n, const int* edges, int64_t k,
                                     DevState* ds, Launch cfg, cudaStream_t s);

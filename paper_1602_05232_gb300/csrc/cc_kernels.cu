@@ -106,7 +106,8 @@ cudaError_t launch_reset(int* parent, int64_t n, int block, cudaStream_t s) {
 template <int E, int VARIANT, bool WARP = false>
 __device__ __forceinline__ int update_edges(int* __restrict__ parent, int n,
                                             const int (&u)[E], const int (&v)[E], int64_t e0,
-                                            int64_t k, DevState* __restrict__ ds, int minhook) {
+                                            int64_t k, DevState* __restrict__ ds, int minhook,
+                                            const unsigned* bits) {
     bool ok[E];
     bool bad = false;
     int made = 0;
@@ -119,6 +120,11 @@ __device__ __forceinline__ int update_edges(int* __restrict__ parent, int n,
         }
     }
     if (bad) flag(ds, ST_RANGE);
+    if (bits) {  // both endpoints in the marked tree: already joined
+#pragma unroll
+        for (int i = 0; i < E; i++)
+            if (ok[i] && big_member(bits, u[i]) && big_member(bits, v[i])) ok[i] = false;
+    }
     if constexpr (VARIANT == 0) {
         int pu[E], pv[E];
 #pragma unroll
@@ -179,7 +185,7 @@ __device__ __forceinline__ int update_edges(int* __restrict__ parent, int n,
 template <int E, int VARIANT, bool WARP>
 __global__ void __launch_bounds__(1024)
 k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
-         DevState* __restrict__ ds, int early, int minhook) {
+         DevState* __restrict__ ds, int early, int minhook, const unsigned* __restrict__ big) {
     pdl_trigger();
     if (!early) pdl_wait();
     int made = 0;
@@ -192,7 +198,7 @@ k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t
             int u[E], v[E];
             load_pairs<E>(edges, e0, k, vec, u, v);
             if (early) pdl_wait();
-            made = update_edges<E, VARIANT, WARP>(parent, n, u, v, e0, k, ds, minhook);
+            made = update_edges<E, VARIANT, WARP>(parent, n, u, v, e0, k, ds, minhook, big_active(big, ds));
         }
     } else {
         // persistent grid: loop over chunks, loading the next chunk's edges
@@ -201,11 +207,12 @@ k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t
         int u[E], v[E];
         if (e0 < k) load_pairs<E>(edges, e0, k, vec, u, v);
         if (early) pdl_wait();
+        const unsigned* bits = big_active(big, ds);
         while (WARP ? __any_sync(0xffffffffu, e0 < k) : e0 < k) {
             const int64_t nx = e0 + stride;
             int nu[E] = {}, nv[E] = {};
             if (nx < k) load_pairs<E>(edges, nx, k, vec, nu, nv);
-            made += update_edges<E, 1, WARP>(parent, n, u, v, e0, k, ds, minhook);
+            made += update_edges<E, 1, WARP>(parent, n, u, v, e0, k, ds, minhook, bits);
 #pragma unroll
             for (int i = 0; i < E; i++) {
                 u[i] = nu[i];
@@ -221,10 +228,11 @@ k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t
 // --- VARIANT 3: the persistent grid with a two-stage prefetch -------------
 
 // Bit i set when this thread's edge i at e0 exists and has both endpoints in
-// range; range errors are flagged here, once per chunk.
+// range, and (with a largest-component bitmap) they are not both marked;
+// range errors are flagged here, once per chunk.
 template <int E>
 __device__ __forceinline__ unsigned edge_mask(int n, const int (&u)[E], const int (&v)[E], int64_t e0,
-                                              int64_t k, DevState* __restrict__ ds) {
+                                              int64_t k, DevState* __restrict__ ds, const unsigned* bits) {
     unsigned m = 0;
     bool bad = false;
 #pragma unroll
@@ -234,6 +242,11 @@ __device__ __forceinline__ unsigned edge_mask(int n, const int (&u)[E], const in
         else bad = true;
     }
     if (bad) flag(ds, ST_RANGE);
+    if (bits) {
+#pragma unroll
+        for (int i = 0; i < E; i++)
+            if (((m >> i) & 1u) && big_member(bits, u[i]) && big_member(bits, v[i])) m &= ~(1u << i);
+    }
     return m;
 }
 
@@ -294,7 +307,7 @@ __device__ __forceinline__ int walk_and_hook(int* parent, unsigned m, const int 
 template <int E, bool WARP>
 __global__ void __launch_bounds__(1024)
 k_update_deep(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
-              DevState* __restrict__ ds, int early, int minhook) {
+              DevState* __restrict__ ds, int early, int minhook, const unsigned* __restrict__ big) {
     pdl_trigger();
     if (!early) pdl_wait();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * E;
@@ -304,12 +317,13 @@ k_update_deep(int* __restrict__ parent, int n, const int* __restrict__ edges, in
     if (e0 < k) load_pairs<E>(edges, e0, k, vec, u0, v0);
     if (e0 + stride < k) load_pairs<E>(edges, e0 + stride, k, vec, u1, v1);
     if (early) pdl_wait();
-    unsigned m0 = e0 < k ? edge_mask<E>(n, u0, v0, e0, k, ds) : 0u;
+    const unsigned* bits = big_active(big, ds);
+    unsigned m0 = e0 < k ? edge_mask<E>(n, u0, v0, e0, k, ds, bits) : 0u;
     int pu0[E], pv0[E];
     gather_parents<E>(parent, m0, u0, v0, pu0, pv0);
     while (WARP ? __any_sync(0xffffffffu, e0 < k) : e0 < k) {
         const int64_t e1 = e0 + stride, e2 = e1 + stride;
-        const unsigned m1 = e1 < k ? edge_mask<E>(n, u1, v1, e1, k, ds) : 0u;
+        const unsigned m1 = e1 < k ? edge_mask<E>(n, u1, v1, e1, k, ds, bits) : 0u;
         int pu1[E], pv1[E];
         gather_parents<E>(parent, m1, u1, v1, pu1, pv1);
         int u2[E] = {}, v2[E] = {};
@@ -330,19 +344,19 @@ k_update_deep(int* __restrict__ parent, int n, const int* __restrict__ edges, in
 template <int E>
 static void update_deep_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
                              int block, const cudaAccessPolicyWindow* window, int pdl, int minhook,
-                             int warphook, cudaStream_t s) {
+                             int warphook, const unsigned* big, cudaStream_t s) {
     int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
     if (warphook) {
         const int64_t cap = resident_grid<k_update_deep<E, true>>(block);
         if (g > cap) g = cap;
         launch_windowed(k_update_deep<E, true>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k,
-                        vec, ds, (int)(pdl == 2), minhook);
+                        vec, ds, (int)(pdl == 2), minhook, big);
         return;
     }
     const int64_t cap = resident_grid<k_update_deep<E, false>>(block);
     if (g > cap) g = cap;
     launch_windowed(k_update_deep<E, false>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k, vec,
-                    ds, (int)(pdl == 2), minhook);
+                    ds, (int)(pdl == 2), minhook, big);
 }
 
 // --- VARIANT 5: per-CTA list of open edges ---------------------------------
@@ -360,7 +374,7 @@ static void update_deep_inst(const int* edges, int64_t k, int vec, int* parent, 
 template <int E>
 __global__ void __launch_bounds__(1024, 1)  // without the minimum, E = 1 and 2 were held to 32 registers and spilled
 k_update_tiles(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
-               DevState* __restrict__ ds, int early, int minhook) {
+               DevState* __restrict__ ds, int early, int minhook, const unsigned* __restrict__ big) {
     extern __shared__ int4 open_list[];  // blockDim.x * E entries: (u, v, parent[u], parent[v])
     __shared__ unsigned n_open[2];
     pdl_trigger();
@@ -375,7 +389,8 @@ k_update_tiles(int* __restrict__ parent, int n, const int* __restrict__ edges, i
     int64_t e0 = t * T + (int64_t)threadIdx.x * E;
     if (t < tiles && e0 < k) load_pairs<E>(edges, e0, k, vec, u, v);
     if (early) pdl_wait();
-    if (t < tiles && e0 < k) m = edge_mask<E>(n, u, v, e0, k, ds);
+    const unsigned* bits = big_active(big, ds);
+    if (t < tiles && e0 < k) m = edge_mask<E>(n, u, v, e0, k, ds, bits);
     gather_parents<E>(parent, m, u, v, pu, pv);
     __syncthreads();  // counters cleared
     const unsigned lane = threadIdx.x & 31u;
@@ -409,7 +424,7 @@ k_update_tiles(int* __restrict__ parent, int n, const int* __restrict__ edges, i
         unsigned m1 = 0;
         if (t1 < tiles && e1 < k) {
             load_pairs<E>(edges, e1, k, vec, nu, nv);
-            m1 = edge_mask<E>(n, nu, nv, e1, k, ds);
+            m1 = edge_mask<E>(n, nu, nv, e1, k, ds, bits);
         }
         int npu[E], npv[E];
         gather_parents<E>(parent, m1, nu, nv, npu, npv);
@@ -434,7 +449,8 @@ k_update_tiles(int* __restrict__ parent, int n, const int* __restrict__ edges, i
 
 template <int E>
 static void update_tiles_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds, int block,
-                              const cudaAccessPolicyWindow* window, int pdl, int minhook, cudaStream_t s) {
+                              const cudaAccessPolicyWindow* window, int pdl, int minhook, const unsigned* big,
+                              cudaStream_t s) {
     const size_t smem = sizeof(int4) * (size_t)block * E;
     if (smem > 48 * 1024)  // the largest list (1024 threads x 4 edges) needs 64 KiB
         cudaFuncSetAttribute(k_update_tiles<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -446,7 +462,7 @@ static void update_tiles_inst(const int* edges, int64_t k, int vec, int* parent,
     const int64_t cap = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
     if (g > cap) g = cap;
     if (!window && !pdl) {
-        k_update_tiles<E><<<(unsigned)g, block, smem, s>>>(parent, n, edges, k, vec, ds, 0, minhook);
+        k_update_tiles<E><<<(unsigned)g, block, smem, s>>>(parent, n, edges, k, vec, ds, 0, minhook, big);
         return;
     }
     cudaLaunchConfig_t cfg = {};
@@ -468,7 +484,7 @@ static void update_tiles_inst(const int* edges, int64_t k, int vec, int* parent,
     }
     cfg.attrs = attr;
     cfg.numAttrs = na;
-    cudaLaunchKernelEx(&cfg, k_update_tiles<E>, parent, n, edges, k, vec, ds, (int)(pdl == 2), minhook);
+    cudaLaunchKernelEx(&cfg, k_update_tiles<E>, parent, n, edges, k, vec, ds, (int)(pdl == 2), minhook, big);
 }
 
 // --- VARIANT 4: filter pass + live-edge pass ------------------------------
@@ -488,7 +504,7 @@ template <int E>
 __global__ void __launch_bounds__(1024)
 k_update_filter(const int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
                 int4* __restrict__ live, unsigned* __restrict__ count, int sel, DevState* __restrict__ ds,
-                int early) {
+                int early, const unsigned* __restrict__ big) {
     pdl_trigger();
     if (!early) pdl_wait();
     const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
@@ -496,7 +512,7 @@ k_update_filter(const int* __restrict__ parent, int n, const int* __restrict__ e
     if (e0 < k) load_pairs<E>(edges, e0, k, vec, u, v);
     if (early) pdl_wait();
     if (blockIdx.x == 0 && threadIdx.x == 0) count[sel ^ 1] = 0u;
-    const unsigned m = e0 < k ? edge_mask<E>(n, u, v, e0, k, ds) : 0u;
+    const unsigned m = e0 < k ? edge_mask<E>(n, u, v, e0, k, ds, big_active(big, ds)) : 0u;
     int pu[E], pv[E];
     gather_parents<E>(parent, m, u, v, pu, pv);
     unsigned open = 0;
@@ -548,10 +564,11 @@ k_update_live(int* __restrict__ parent, const int4* __restrict__ live, const uns
 template <int E>
 static void update_filter_inst(const int* edges, int64_t k, int vec, const int* parent, int n, int4* live,
                                unsigned* count, int sel, DevState* ds, int block,
-                               const cudaAccessPolicyWindow* window, int pdl, cudaStream_t s) {
+                               const cudaAccessPolicyWindow* window, int pdl, const unsigned* big,
+                               cudaStream_t s) {
     const int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
     launch_windowed(k_update_filter<E>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k, vec,
-                    live, count, sel, ds, (int)(pdl == 2));
+                    live, count, sel, ds, (int)(pdl == 2), big);
 }
 
 cudaError_t launch_update_split(int* parent, int n, const int* edges, int64_t k, DevState* ds, Launch cfg,
@@ -559,9 +576,9 @@ cudaError_t launch_update_split(int* parent, int n, const int* edges, int64_t k,
     if (k <= 0) return cudaSuccess;
     const int vec = pair_vec(edges);
     switch (cfg.ept) {
-        case 1: update_filter_inst<1>(edges, k, vec, parent, n, live, count, sel, ds, cfg.block, cfg.window, cfg.pdl, s); break;
-        case 2: update_filter_inst<2>(edges, k, vec, parent, n, live, count, sel, ds, cfg.block, cfg.window, cfg.pdl, s); break;
-        case 4: update_filter_inst<4>(edges, k, vec, parent, n, live, count, sel, ds, cfg.block, cfg.window, cfg.pdl, s); break;
+        case 1: update_filter_inst<1>(edges, k, vec, parent, n, live, count, sel, ds, cfg.block, cfg.window, cfg.pdl, cfg.big, s); break;
+        case 2: update_filter_inst<2>(edges, k, vec, parent, n, live, count, sel, ds, cfg.block, cfg.window, cfg.pdl, cfg.big, s); break;
+        case 4: update_filter_inst<4>(edges, k, vec, parent, n, live, count, sel, ds, cfg.block, cfg.window, cfg.pdl, cfg.big, s); break;
         default: return cudaErrorInvalidValue;
     }
     cudaError_t e = cudaGetLastError();
@@ -586,32 +603,32 @@ cudaError_t launch_update_split(int* parent, int n, const int* edges, int64_t k,
 template <int E, int VARIANT, bool WARP>
 static void update_inst2(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
                          int block, const cudaAccessPolicyWindow* window, int pdl, int minhook,
-                         cudaStream_t s) {
+                         const unsigned* big, cudaStream_t s) {
     int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
     if (VARIANT == 2) {
         const int64_t cap = resident_grid<k_update<E, VARIANT, WARP>>(block);
         if (g > cap) g = cap;
     }
     launch_windowed(k_update<E, VARIANT, WARP>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k,
-                    vec, ds, (int)(pdl == 2), minhook);
+                    vec, ds, (int)(pdl == 2), minhook, big);
 }
 
 // warphook applies to the lockstep variants (1, 2); variant 0 hooks per edge
 template <int E, int VARIANT>
 static void update_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
                         int block, const cudaAccessPolicyWindow* window, int pdl, int minhook,
-                        int warphook, cudaStream_t s) {
+                        int warphook, const unsigned* big, cudaStream_t s) {
     if (VARIANT != 0 && warphook)
-        update_inst2<E, VARIANT, VARIANT != 0>(edges, k, vec, parent, n, ds, block, window, pdl, minhook, s);
+        update_inst2<E, VARIANT, VARIANT != 0>(edges, k, vec, parent, n, ds, block, window, pdl, minhook, big, s);
     else
-        update_inst2<E, VARIANT, false>(edges, k, vec, parent, n, ds, block, window, pdl, minhook, s);
+        update_inst2<E, VARIANT, false>(edges, k, vec, parent, n, ds, block, window, pdl, minhook, big, s);
 }
 
 cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevState* ds,
                           Launch cfg, cudaStream_t s) {
     if (k <= 0) return cudaSuccess;
     const int vec = pair_vec(edges);
-#define CC_UPD(E, V) update_inst<E, V>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, s)
+#define CC_UPD(E, V) update_inst<E, V>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, cfg.big, s)
     switch (cfg.variant * 8 + cfg.ept) {
         case 1: CC_UPD(1, 0); break;
         case 2: CC_UPD(2, 0); break;
@@ -622,12 +639,12 @@ cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevSt
         case 17: CC_UPD(1, 2); break;
         case 18: CC_UPD(2, 2); break;
         case 20: CC_UPD(4, 2); break;
-        case 25: update_deep_inst<1>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, s); break;
-        case 26: update_deep_inst<2>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, s); break;
-        case 28: update_deep_inst<4>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, s); break;
-        case 41: update_tiles_inst<1>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, s); break;
-        case 42: update_tiles_inst<2>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, s); break;
-        case 44: update_tiles_inst<4>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, s); break;
+        case 25: update_deep_inst<1>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, cfg.big, s); break;
+        case 26: update_deep_inst<2>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, cfg.big, s); break;
+        case 28: update_deep_inst<4>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, cfg.big, s); break;
+        case 41: update_tiles_inst<1>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.big, s); break;
+        case 42: update_tiles_inst<2>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.big, s); break;
+        case 44: update_tiles_inst<4>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.big, s); break;
         default: return cudaErrorInvalidValue;
     }
 #undef CC_UPD
@@ -657,11 +674,14 @@ __device__ __forceinline__ void store_answers(uint8_t* __restrict__ out, int64_t
 }
 
 // One chunk of Algorithm 1: the E pairs (u, v) of this thread, answers in a.
-// Returns whether a pair had an id outside [0, n). MODE as for k_query.
+// Returns whether a pair had an id outside [0, n). MODE as for k_query. With
+// a largest-component bitmap, a pair whose endpoints are both marked is
+// answered 1 from the bitmap alone: it reads no parent and walks nothing
+// (its first parents are set equal, which every MODE below answers with 1).
 template <int E, int MODE>
 __device__ __forceinline__ bool query_chunk(int* __restrict__ parent, int n, int (&u)[E], int (&v)[E],
                                             int64_t e0, int64_t k, uint8_t (&a)[E],
-                                            DevState* __restrict__ ds) {
+                                            DevState* __restrict__ ds, const unsigned* bits) {
     bool ok[E];
     bool bad = false;
 #pragma unroll
@@ -673,10 +693,15 @@ __device__ __forceinline__ bool query_chunk(int* __restrict__ parent, int n, int
         }
         if (!ok[i]) { u[i] = 0; v[i] = 0; }
     }
+    bool hit[E];
+#pragma unroll
+    for (int i = 0; i < E; i++) hit[i] = bits && ok[i] && big_member(bits, u[i]) && big_member(bits, v[i]);
     int pu[E], pv[E];
 #pragma unroll
     for (int i = 0; i < E; i++) {
-        if (MODE == 1 || MODE == 3) {
+        if (hit[i]) {
+            pu[i] = pv[i] = u[i];
+        } else if (MODE == 1 || MODE == 3) {
             pu[i] = parent[u[i]];
             pv[i] = parent[v[i]];
         } else {
@@ -754,7 +779,8 @@ __device__ __forceinline__ bool query_chunk(int* __restrict__ parent, int n, int
 template <int E, int MODE, bool PERSIST>
 __global__ void __launch_bounds__(1024)
 k_query(int* __restrict__ parent, int n, const int* __restrict__ pairs, int64_t k, int vec,
-        uint8_t* __restrict__ out, int ovec, DevState* __restrict__ ds, int early) {
+        uint8_t* __restrict__ out, int ovec, DevState* __restrict__ ds, int early,
+        const unsigned* __restrict__ big) {
     pdl_trigger();
     if (!early) pdl_wait();
     int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
@@ -764,8 +790,9 @@ k_query(int* __restrict__ parent, int n, const int* __restrict__ pairs, int64_t 
     uint8_t a[E];
     load_pairs<E>(pairs, e0, k, vec, u, v);
     if (early) pdl_wait();
+    const unsigned* bits = big_active(big, ds);
     if (!PERSIST) {
-        bad = query_chunk<E, MODE>(parent, n, u, v, e0, k, a, ds);
+        bad = query_chunk<E, MODE>(parent, n, u, v, e0, k, a, ds, bits);
         store_answers<E>(out, e0, k, ovec != 0, a);
     } else {
         const int64_t stride = (int64_t)gridDim.x * blockDim.x * E;
@@ -773,7 +800,7 @@ k_query(int* __restrict__ parent, int n, const int* __restrict__ pairs, int64_t 
             const int64_t nx = e0 + stride;
             int nu[E] = {}, nv[E] = {};
             if (nx < k) load_pairs<E>(pairs, nx, k, vec, nu, nv);
-            bad |= query_chunk<E, MODE>(parent, n, u, v, e0, k, a, ds);
+            bad |= query_chunk<E, MODE>(parent, n, u, v, e0, k, a, ds, bits);
             store_answers<E>(out, e0, k, ovec != 0, a);
 #pragma unroll
             for (int i = 0; i < E; i++) {
@@ -892,19 +919,19 @@ k_query_warp(const int* __restrict__ parent, int n, const int* __restrict__ pair
 template <int E, int MODE, bool PERSIST>
 static void query_one(unsigned g, int block, const cudaAccessPolicyWindow* window, int pdl, cudaStream_t s,
                       int* parent, int n, const int* pairs, int64_t k, int vec, uint8_t* out, int ovec,
-                      DevState* ds) {
+                      DevState* ds, const unsigned* big) {
     if (PERSIST) {
         const int c = resident_grid<k_query<E, MODE, PERSIST>>(block);
         if (g > (unsigned)c) g = (unsigned)c;
     }
     launch_windowed(k_query<E, MODE, PERSIST>, g, block, s, window, pdl != 0, parent, n, pairs, k, vec, out, ovec,
-                    ds, (int)(pdl == 2));
+                    ds, (int)(pdl == 2), big);
 }
 
 template <int MODE>
 static void query_inst(unsigned g, Launch cfg, cudaStream_t s, int* parent, int n,
                        const int* pairs, int64_t k, int vec, uint8_t* out, int ovec, DevState* ds) {
-#define CC_Q(E, P) query_one<E, MODE, P>(g, cfg.block, cfg.window, cfg.pdl, s, parent, n, pairs, k, vec, out, ovec, ds)
+#define CC_Q(E, P) query_one<E, MODE, P>(g, cfg.block, cfg.window, cfg.pdl, s, parent, n, pairs, k, vec, out, ovec, ds, cfg.big)
     const bool persist = cfg.query_variant == 1;
     switch (cfg.ept) {
         case 1: if (persist) CC_Q(1, true); else CC_Q(1, false); break;
@@ -945,12 +972,17 @@ cudaError_t launch_query(int* parent, int n, const int* pairs, int64_t k, uint8_
 // entries that change are written. With OUT, the roots are also written to
 // out[] -- the minimum-id labels, since the root is the smallest id of its
 // tree. No hooks run concurrently, so the roots are fixed for the whole pass.
-template <bool OUT>
+// With BIG, the pass also rewrites the largest-component bitmap: bit v = (the
+// root of v is ds->big_root), one 32-bit word per 8 lanes (a warp covers 128
+// consecutive vertices); every lane of a warp takes part, so threads past n
+// do not leave early. (Counting the marked vertices here, one atomic per warp
+// on one word, doubled the pass: launch_big_count does it on demand.)
+template <bool OUT, bool BIG>
 __global__ void __launch_bounds__(1024)
 k_compress_all(int* __restrict__ parent, int64_t n, int* __restrict__ out,
-               DevState* __restrict__ ds) {
+               DevState* __restrict__ ds, unsigned* __restrict__ big) {
     const int64_t v0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    if (v0 >= n) return;
+    if (!BIG && v0 >= n) return;
     const bool full = v0 + 4 <= n;
     int p0[4], x[4], p[4];
     if (full) {
@@ -958,11 +990,11 @@ k_compress_all(int* __restrict__ parent, int64_t n, int* __restrict__ out,
         p0[0] = q.x; p0[1] = q.y; p0[2] = q.z; p0[3] = q.w;
     } else {
 #pragma unroll
-        for (int i = 0; i < 4; i++) p0[i] = v0 + i < n ? parent[v0 + i] : (int)(v0 + i);
+        for (int i = 0; i < 4; i++) p0[i] = v0 + i < n ? parent[v0 + i] : 0;
     }
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        x[i] = (int)(v0 + i);
+        x[i] = v0 + i < n ? (int)(v0 + i) : 0;  // past n: a walk of length 0
         p[i] = p0[i];
     }
     while (true) {
@@ -991,21 +1023,128 @@ k_compress_all(int* __restrict__ parent, int64_t n, int* __restrict__ out,
                 if (v0 + i < n) out[v0 + i] = x[i];
         }
     }
+    if (BIG) {
+        const int R = ds->big_root;  // the same for every thread
+        if (R < 0) return;
+        unsigned nib = 0;
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            if (v0 + i < n && x[i] == R) nib |= 1u << i;
+        const unsigned lane = threadIdx.x & 31u;
+        unsigned w = nib << ((lane & 7u) * 4u);
+        w |= __shfl_xor_sync(0xffffffffu, w, 1);
+        w |= __shfl_xor_sync(0xffffffffu, w, 2);
+        w |= __shfl_xor_sync(0xffffffffu, w, 4);
+        if ((lane & 7u) == 0 && v0 < n) big[v0 >> 5] = w;  // word v0 / 32 holds vertices v0 .. v0 + 31
+    }
+}
+
+// ds->big_members += the set bits of words[0, nwords): one atomic per CTA.
+__global__ void __launch_bounds__(256)
+k_big_count(const unsigned* __restrict__ words, int64_t nwords, DevState* __restrict__ ds) {
+    __shared__ unsigned part[8];
+    unsigned c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += (int64_t)gridDim.x * blockDim.x)
+        c += (unsigned)__popc(words[i]);
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[w];
+        if (t) atomicAdd(&ds->big_members, t);
+    }
+}
+
+cudaError_t launch_big_count(const unsigned* words, int64_t nwords, DevState* ds, cudaStream_t s) {
+    if (nwords <= 0) return cudaSuccess;
+    int64_t g = (nwords + 255) / 256;
+    if (g > 1024) g = 1024;
+    k_big_count<<<(unsigned)g, 256, 0, s>>>(words, nwords, ds);
+    return cudaGetLastError();
+}
+
+// The root of the largest tree, estimated (the sampling step of Afforest's
+// large-component skip): kBigSample vertices, spread over [0, n) by the
+// golden-ratio sequence, are walked to their roots (read-only); the roots go
+// into a shared-memory hash table with a count each, and the most frequent
+// one (the smaller id on a tie) becomes ds->big_root if at least min_share of
+// the sample reached it, else -1. One CTA of kBigSample threads.
+__global__ void __launch_bounds__(kBigSample)
+k_big_pick(const int* __restrict__ parent, int64_t n, int min_share, DevState* __restrict__ ds) {
+    constexpr int kSlots = 2 * kBigSample;
+    __shared__ int key[kSlots];
+    __shared__ int cnt[kSlots];
+    __shared__ unsigned long long best[kBigSample / 32];
+    const int t = threadIdx.x;
+    for (int i = t; i < kSlots; i += blockDim.x) {
+        key[i] = -1;
+        cnt[i] = 0;
+    }
+    // x = floor(frac((t + 1) * phi) * n), in [0, n)
+    const uint64_t h = (uint64_t)(t + 1) * 0x9E3779B97F4A7C15ull;
+    const int x = (int)(((h >> 32) * (uint64_t)n) >> 32);
+    const int r = walk_root(parent, x, parent[x]);
+    __syncthreads();
+    unsigned slot = ((unsigned)r * 0x9E3779B1u) >> 21;  // 11 bits: kSlots slots
+    for (int probe = 0; probe < kSlots; probe++) {       // at most kBigSample keys: a free slot exists
+        const int prev = atomicCAS(&key[slot], -1, r);
+        if (prev == -1 || prev == r) {
+            atomicAdd(&cnt[slot], 1);
+            break;
+        }
+        slot = (slot + 1) & (kSlots - 1);
+    }
+    __syncthreads();
+    // (count, then the smaller id) as one 64-bit key; the maximum wins
+    unsigned long long mine = 0;
+    for (int i = t; i < kSlots; i += blockDim.x)
+        if (cnt[i]) {
+            const unsigned long long c = ((unsigned long long)cnt[i] << 32) | (unsigned)(0x7fffffff - key[i]);
+            if (c > mine) mine = c;
+        }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, mine, d);
+        if (o > mine) mine = o;
+    }
+    if ((t & 31) == 0) best[t >> 5] = mine;
+    __syncthreads();
+    if (t == 0) {
+        unsigned long long b = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++)
+            if (best[w] > b) b = best[w];
+        const int count = (int)(b >> 32);
+        const int root = 0x7fffffff - (int)(b & 0xffffffffu);
+        ds->big_root = (b && count >= min_share) ? root : -1;
+    }
+}
+
+cudaError_t launch_big_pick(const int* parent, int64_t n, int min_share, DevState* ds, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_big_pick<<<1, kBigSample, 0, s>>>(parent, n, min_share, ds);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_compress_all(int* parent, int64_t n, int* out, DevState* ds, int block,
-                                cudaStream_t s) {
+                                cudaStream_t s, unsigned* big) {
     const unsigned g = blocks_for(n, 4LL * block);
     const bool aligned_out = out && reinterpret_cast<uintptr_t>(out) % 16 == 0;
     if (out && !aligned_out) {
         // labels into a buffer without 16-byte alignment: compress, then copy
-        k_compress_all<false><<<g, block, 0, s>>>(parent, n, nullptr, ds);
+        if (big) k_compress_all<false, true><<<g, block, 0, s>>>(parent, n, nullptr, ds, big);
+        else k_compress_all<false, false><<<g, block, 0, s>>>(parent, n, nullptr, ds, nullptr);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         return cudaMemcpyAsync(out, parent, (size_t)n * sizeof(int), cudaMemcpyDeviceToDevice, s);
     }
-    if (out) k_compress_all<true><<<g, block, 0, s>>>(parent, n, out, ds);
-    else k_compress_all<false><<<g, block, 0, s>>>(parent, n, nullptr, ds);
+    if (out) {
+        if (big) k_compress_all<true, true><<<g, block, 0, s>>>(parent, n, out, ds, big);
+        else k_compress_all<true, false><<<g, block, 0, s>>>(parent, n, out, ds, nullptr);
+    } else {
+        if (big) k_compress_all<false, true><<<g, block, 0, s>>>(parent, n, nullptr, ds, big);
+        else k_compress_all<false, false><<<g, block, 0, s>>>(parent, n, nullptr, ds, nullptr);
+    }
     return cudaGetLastError();
 }
 

@@ -38,7 +38,7 @@ PLAIN_SPACE = {
     "update_variant": [0, 1, 2, 3, 4, 5],
     "edges_per_thread": [1, 2, 4],
     "block": [128, 256, 512, 1024],
-    "compress_every": [0, 1, 2, 4, 8, 16],
+    "compress_every": [0, 1, 2, 3, 4, 6, 8, 16],
     "compress_scope": [0, 1],
     "query_halving": [0, 1, 2],
     "l2_persist": [0, 1],
@@ -48,10 +48,12 @@ PLAIN_SPACE = {
     "hook": [0, 1, 2],
     "edge_order": [0, 7, 9],
     "hook_warp": [0, 1],
+    "big_filter": [0, 384, 640, 896],
 }
 PLAIN_START = {"update_variant": 0, "edges_per_thread": 2, "block": 256, "compress_every": 1,
                "compress_scope": 0, "query_halving": 0, "l2_persist": 0, "query_variant": 0,
-               "pdl": 1, "query_pairs_per_thread": 0, "hook": 0, "edge_order": 0, "hook_warp": 0}
+               "pdl": 1, "query_pairs_per_thread": 0, "hook": 0, "edge_order": 0, "hook_warp": 0,
+               "big_filter": 0}
 
 SEG_SPACE = {
     "seg_block": [128, 256, 512, 1024],
@@ -183,10 +185,20 @@ class PlainBench:
         return statistics.median(times)
 
 
+def canonical_plain(options: dict) -> dict:
+    """The same launch with options that cannot act set to their defaults: the
+    largest-component filter is built only by full compression passes."""
+    o = dict(options)
+    if o.get("compress_every", 1) == 0 or o.get("compress_scope", 0) == 1:
+        o["big_filter"] = 0
+    return o
+
+
 def tune_plain(stream_obj, space=PLAIN_SPACE, start=PLAIN_START, repeats: int = 3, log=None):
     """start: one option dict or a list of them (see coordinate_descent)."""
     bench = PlainBench(stream_obj)
-    return coordinate_descent(space, start, lambda o: bench.time(o, repeats), log=log)
+    best, t, table = coordinate_descent(space, start, lambda o: bench.time(o, repeats), log=log)
+    return canonical_plain(best), t, table
 
 
 # ---------------------------------------------------------- batched form

@@ -88,6 +88,25 @@ OPTION_SETS = {
     "warp_query_flat_b1024": {"query_variant": 2, "compress_every": 1, "block": 1024},
     "warp_query_halving_ignored_pdl2": {"query_variant": 2, "query_halving": 1, "compress_every": 3, "pdl": 2,
                                         "block": 64},
+    # largest-component filter: the bitmap written by full compressions
+    "big_default": {"big_filter": 256},
+    "big_every1_flat_query": {"big_filter": 1, "compress_every": 1},
+    "big_cta_list_ordered_min": {"big_filter": 128, "update_variant": 5, "edges_per_thread": 2, "edge_order": 7,
+                                 "compress_every": 2, "hook": 1, "pdl": 2},
+    "big_cta_list_ept1": {"big_filter": 1, "update_variant": 5, "edges_per_thread": 1, "block": 128,
+                          "compress_every": 3},
+    "big_persistent_query_halving": {"big_filter": 64, "query_variant": 1, "query_halving": 1, "compress_every": 3},
+    "big_splitting_query": {"big_filter": 64, "query_halving": 2, "compress_every": 2, "update_variant": 2,
+                            "edges_per_thread": 1},
+    "big_deep_pdl2": {"big_filter": 32, "update_variant": 3, "edges_per_thread": 4, "pdl": 2, "compress_every": 2},
+    "big_two_pass": {"big_filter": 16, "update_variant": 4, "edges_per_thread": 2, "compress_every": 2},
+    "big_lockstep_warp_hook": {"big_filter": 1, "update_variant": 1, "hook_warp": 1, "compress_every": 1,
+                               "edges_per_thread": 4},
+    "big_per_edge_query_ept4": {"big_filter": 1, "update_variant": 0, "compress_every": 2,
+                                "query_pairs_per_thread": 4},
+    "big_warp_query": {"big_filter": 1, "query_variant": 2, "compress_every": 1},
+    "big_all_samples": {"big_filter": 1024, "compress_every": 1},
+    "big_touched_scope_never_built": {"big_filter": 1, "compress_scope": 1},
 }
 
 
@@ -151,7 +170,9 @@ def test_uniform_small_every_batch(cc, opts):
                                   "warp_hook_lockstep", "warp_hook_persistent_min", "warp_hook_deep_first_min",
                                   "warp_hook_two_pass", "warp_hook_ordered", "warp_query", "cta_list_ept1_b128",
                                   "cta_list_ept2_min", "cta_list_ept4_b1024",
-                                  "warp_query_halving_ignored_pdl2"])
+                                  "warp_query_halving_ignored_pdl2", "big_default", "big_every1_flat_query",
+                                  "big_cta_list_ordered_min", "big_persistent_query_halving", "big_deep_pdl2",
+                                  "big_two_pass", "big_lockstep_warp_hook"])
 def test_rmat_small(cc, opts):
     s = I.rmat_stream(scale=16, m=1 << 20, batch=(1 << 16) + 3, q=(1 << 16) - 5, seed=1)
     run_stream(cc, s, OPTION_SETS[opts], label_every=4, check_invariants=True)
@@ -162,7 +183,10 @@ def test_rmat_small(cc, opts):
                                   "deep_prefetch_ept1_b1024", "two_pass_ept1_pdl0", "min_hook",
                                   "min_hook_deep", "order8", "order9_persistent_pdl2", "order9_two_pass",
                                   "warp_hook_deep_ept1", "warp_hook_two_pass_min", "warp_hook_ordered",
-                                  "warp_query", "warp_query_flat_b1024", "cta_list_ept1_b128", "cta_list_ordered"])
+                                  "warp_query", "warp_query_flat_b1024", "cta_list_ept1_b128", "cta_list_ordered",
+                                  "big_default", "big_every1_flat_query", "big_cta_list_ordered_min",
+                                  "big_cta_list_ept1", "big_splitting_query", "big_per_edge_query_ept4",
+                                  "big_warp_query", "big_all_samples"])
 def test_grid_small(cc, opts):
     s = I.grid_stream(512, 512, batch=(1 << 14) + 1, q=1 << 14, seed=2)
     ref = run_stream(cc, s, OPTION_SETS[opts], label_every=8, check_invariants=True)
@@ -323,6 +347,7 @@ OPTION_RANGES = [
     ("sv_graph", [-1, 2], [0, 1]),
     ("edge_order", [-1, 1, 5, 10], [0, 6, 9]),
     ("hook_warp", [-1, 2], [0, 1]),
+    ("big_filter", [-1, 1025], [0, 1, 1024]),
 ]
 
 

@@ -61,3 +61,12 @@ def test_starts_include_the_stored_result(monkeypatch):
     assert tune.starts_for("w", space, default) == [default]     # value no longer in the space
     monkeypatch.setattr(tune, "tuned_options", lambda wl, device=None: None)
     assert tune.starts_for("w", space, default) == [default]
+
+
+def test_canonical_plain_drops_a_filter_nothing_builds():
+    o = {"compress_every": 0, "compress_scope": 0, "big_filter": 896, "block": 128}
+    assert tune.canonical_plain(o) == {"compress_every": 0, "compress_scope": 0, "big_filter": 0, "block": 128}
+    o = {"compress_every": 4, "compress_scope": 1, "big_filter": 640}
+    assert tune.canonical_plain(o)["big_filter"] == 0
+    o = {"compress_every": 6, "compress_scope": 0, "big_filter": 640}
+    assert tune.canonical_plain(o) == o
