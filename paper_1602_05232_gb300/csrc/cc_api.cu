@@ -265,7 +265,7 @@ cc::Launch update_cfg(const cc_ctx* c, bool first) {
 
 // One Bulk-Update as a filter pass and a live-edge pass (update variant 4).
 // The list has room for k entries; growing it synchronises the stream once.
-cc_status split_update(cc_ctx* c, const int32_t* edges, int64_t k, bool first, bool ordered) {
+cc_status split_update(cc_ctx* c, const int32_t* edges, int64_t k, bool first, bool ordered, const int32_t* alt) {
     cudaError_t e = cudaSuccess;
     if (!c->live_count) {
         e = cudaMalloc(&c->live_count, 2 * sizeof(unsigned));
@@ -292,6 +292,7 @@ cc_status split_update(cc_ctx* c, const int32_t* edges, int64_t k, bool first, b
     const int sel = (int)(c->live_seq & 1u);
     cc::Launch cfg = update_cfg(c, first);
     if (ordered && cfg.pdl == 2) cfg.pdl = 1;  // its edges were written by the kernel just before
+    cfg.alt = alt;
     cc_status s = run(c, CC_K_UPDATE, "bulk_update (two passes)", [&] {
         return cc::launch_update_split(c->parent, (int)c->n, edges, k, c->ds, cfg, c->live,
                                        c->live_count, sel, c->stream);
@@ -307,7 +308,10 @@ cc_status split_update(cc_ctx* c, const int32_t* edges, int64_t k, bool first, b
 // handle's scratch copy, which then replaces `edges` for the update. The
 // scratch grows to the largest minibatch with one stream synchronisation;
 // its bucket counters start at zero and every call leaves them at zero.
-cc_status order_edges(cc_ctx* c, const int32_t** edges, int64_t k) {
+// skip_big: the largest-component bitmap when the update kernel that follows
+// takes the caller's edges as BigArgs::alt; the order kernels then do nothing
+// while the bitmap is in use.
+cc_status order_edges(cc_ctx* c, const int32_t** edges, int64_t k, const unsigned* skip_big) {
     const int b = (int)c->opt[CC_OPT_EDGE_ORDER];
     const int64_t counters = cc::order_counter_ints(b);
     if (k > c->order_cap || counters > c->order_hist_cap || c->order_dirty) {
@@ -342,7 +346,7 @@ cc_status order_edges(cc_ctx* c, const int32_t** edges, int64_t k) {
     int kernels = 1;
     cc_status s = run(c, CC_K_ORDER, "edge order", [&] {
         return cc::launch_order_edges(*edges, k, (int)c->n, b, c->order_hist, c->order_buf,
-                                      (int)c->opt[CC_OPT_PDL], c->stream, &kernels);
+                                      (int)c->opt[CC_OPT_PDL], c->stream, &kernels, skip_big, c->ds);
     });
     if (s != CC_OK) {
         c->order_dirty = true;  // the counters may be left non-zero
@@ -664,20 +668,27 @@ cc_status cc_bulk_update(cc_ctx* c, const int32_t* edges, int64_t k) {
     if (by_size(c) && c->opt[CC_OPT_UPDATE_SCHEDULE] != 1)
         return fail(CC_ERR_UNSUPPORTED, "union by size (CC_OPT_LINK = 1) needs CC_OPT_UPDATE_SCHEDULE = 1");
     const bool first = c->fresh;  // the forest has no edge yet
+    const int32_t* given = edges;
+    const bool fused = c->opt[CC_OPT_UPDATE_SCHEDULE] != 1;
+    // the fused kernels read the caller's edges instead of an ordered copy
+    // while the largest-component bitmap is in use (cc::BigArgs)
+    const unsigned* big = fused ? cfg_of(c).big : nullptr;
     bool ordered = false;
     if (c->opt[CC_OPT_EDGE_ORDER] > 0 && k >= kOrderMinEdges) {
-        s = order_edges(c, &edges, k);
+        s = order_edges(c, &edges, k, big);
         if (s != CC_OK) return s;
         ordered = true;
     }
+    const int32_t* alt = ordered && big ? given : nullptr;
     c->fresh = false;
-    if (c->opt[CC_OPT_UPDATE_SCHEDULE] == 1) {
+    if (!fused) {
         s = paper_update(c, edges, k);
     } else if (c->opt[CC_OPT_UPDATE_VARIANT] == 4) {
-        s = split_update(c, edges, k, first, ordered);
+        s = split_update(c, edges, k, first, ordered, alt);
     } else {
         cc::Launch cfg = update_cfg(c, first);
         if (ordered && cfg.pdl == 2) cfg.pdl = 1;  // its edges were written by the kernel just before
+        cfg.alt = alt;
         s = run(c, CC_K_UPDATE, "bulk_update", [&] {
             return cc::launch_update(c->parent, (int)c->n, edges, k, c->ds, cfg, c->stream);
         });
@@ -687,7 +698,7 @@ cc_status cc_bulk_update(cc_ctx* c, const int32_t* edges, int64_t k) {
     c->update_calls++;
     const int64_t every = c->opt[CC_OPT_COMPRESS_EVERY];
     if (every > 0 && c->update_calls % (uint64_t)every == 0)
-        return do_compress(c, (int)c->opt[CC_OPT_COMPRESS_SCOPE], edges, k);
+        return do_compress(c, (int)c->opt[CC_OPT_COMPRESS_SCOPE], given, k);  // a set: same endpoints
     return CC_OK;
 }
 

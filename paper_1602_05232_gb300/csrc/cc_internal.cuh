@@ -44,6 +44,21 @@ struct Launch {
     int warphook = 0; // 1: the hooks of a warp are grouped by target root (hook_warp); lockstep variants
     const unsigned* big = nullptr;  // largest-component bitmap (n bits), or none: pairs whose two
                                     // endpoints are marked are answered / dropped without walks
+    const int* alt = nullptr;       // Bulk-Update on an ordered copy: the caller's edges, which the
+                                    // update reads instead while the bitmap is in use (see BigArgs)
+};
+
+// What the fused Bulk-Update kernels take of the largest-component filter.
+// While the bitmap marks a tree (big != null, DevState::big_root >= 0) most
+// edges are dropped before their parent reads, and ordering them no longer
+// pays: launch_order_edges given the same `big` then does nothing, and an
+// update kernel given the ordered copy reads the caller's edges, `alt`,
+// instead. Both decide from big_root, which only the pick kernel writes, and
+// a full compression pass, launched without programmatic dependence, always
+// follows the pick, so every later kernel reads its final value.
+struct BigArgs {
+    const unsigned* big = nullptr;
+    const int* alt = nullptr;
 };
 
 // Alignment class of a pair array: 2 = 16-byte, 1 = 8-byte, 0 = 4-byte.
@@ -98,11 +113,14 @@ cudaError_t launch_compress_touched(int* parent, int n, const int* edges, int64_
 // into 2^b buckets (b <= 9). counters: order_counter_ints(b) ints, all zero
 // before the first call; each call leaves them zero again. pdl as for the
 // update kernel (programmatic dependent launch: 0 off, 1 wait first, 2 read
-// the edges first). *kernels = the number of kernels launched.
+// the edges first). *kernels = the number of kernels launched. With `big`
+// (see BigArgs), both kernels return at once while ds->big_root >= 0, and
+// `out` is left unwritten.
 int order_shift(int64_t n, int log_buckets);
 int64_t order_counter_ints(int log_buckets);
 cudaError_t launch_order_edges(const int* edges, int64_t k, int n, int log_buckets, int* counters,
-                               int* out, int pdl, cudaStream_t s, int* kernels);
+                               int* out, int pdl, cudaStream_t s, int* kernels,
+                               const unsigned* big = nullptr, const DevState* ds = nullptr);
 
 // ---- batched form (segmented forests, one persistent kernel) ----
 

@@ -185,9 +185,13 @@ __device__ __forceinline__ int update_edges(int* __restrict__ parent, int n,
 template <int E, int VARIANT, bool WARP>
 __global__ void __launch_bounds__(1024)
 k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
-         DevState* __restrict__ ds, int early, int minhook, const unsigned* __restrict__ big) {
+         DevState* __restrict__ ds, int early, int minhook, BigArgs fb) {
     pdl_trigger();
     if (!early) pdl_wait();
+    if (fb.alt && big_active(fb.big, ds)) {  // the filter is on: the edges were not ordered
+        edges = fb.alt;
+        vec = pair_vec_dev(fb.alt);
+    }
     int made = 0;
     int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
     if (VARIANT < 2) {
@@ -198,7 +202,7 @@ k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t
             int u[E], v[E];
             load_pairs<E>(edges, e0, k, vec, u, v);
             if (early) pdl_wait();
-            made = update_edges<E, VARIANT, WARP>(parent, n, u, v, e0, k, ds, minhook, big_active(big, ds));
+            made = update_edges<E, VARIANT, WARP>(parent, n, u, v, e0, k, ds, minhook, big_active(fb.big, ds));
         }
     } else {
         // persistent grid: loop over chunks, loading the next chunk's edges
@@ -207,7 +211,7 @@ k_update(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t
         int u[E], v[E];
         if (e0 < k) load_pairs<E>(edges, e0, k, vec, u, v);
         if (early) pdl_wait();
-        const unsigned* bits = big_active(big, ds);
+        const unsigned* bits = big_active(fb.big, ds);
         while (WARP ? __any_sync(0xffffffffu, e0 < k) : e0 < k) {
             const int64_t nx = e0 + stride;
             int nu[E] = {}, nv[E] = {};
@@ -307,9 +311,13 @@ __device__ __forceinline__ int walk_and_hook(int* parent, unsigned m, const int 
 template <int E, bool WARP>
 __global__ void __launch_bounds__(1024)
 k_update_deep(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
-              DevState* __restrict__ ds, int early, int minhook, const unsigned* __restrict__ big) {
+              DevState* __restrict__ ds, int early, int minhook, BigArgs fb) {
     pdl_trigger();
     if (!early) pdl_wait();
+    if (fb.alt && big_active(fb.big, ds)) {  // as in k_update
+        edges = fb.alt;
+        vec = pair_vec_dev(fb.alt);
+    }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * E;
     int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
     int made = 0;
@@ -317,7 +325,7 @@ k_update_deep(int* __restrict__ parent, int n, const int* __restrict__ edges, in
     if (e0 < k) load_pairs<E>(edges, e0, k, vec, u0, v0);
     if (e0 + stride < k) load_pairs<E>(edges, e0 + stride, k, vec, u1, v1);
     if (early) pdl_wait();
-    const unsigned* bits = big_active(big, ds);
+    const unsigned* bits = big_active(fb.big, ds);
     unsigned m0 = e0 < k ? edge_mask<E>(n, u0, v0, e0, k, ds, bits) : 0u;
     int pu0[E], pv0[E];
     gather_parents<E>(parent, m0, u0, v0, pu0, pv0);
@@ -344,19 +352,19 @@ k_update_deep(int* __restrict__ parent, int n, const int* __restrict__ edges, in
 template <int E>
 static void update_deep_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
                              int block, const cudaAccessPolicyWindow* window, int pdl, int minhook,
-                             int warphook, const unsigned* big, cudaStream_t s) {
+                             int warphook, BigArgs fb, cudaStream_t s) {
     int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
     if (warphook) {
         const int64_t cap = resident_grid<k_update_deep<E, true>>(block);
         if (g > cap) g = cap;
         launch_windowed(k_update_deep<E, true>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k,
-                        vec, ds, (int)(pdl == 2), minhook, big);
+                        vec, ds, (int)(pdl == 2), minhook, fb);
         return;
     }
     const int64_t cap = resident_grid<k_update_deep<E, false>>(block);
     if (g > cap) g = cap;
     launch_windowed(k_update_deep<E, false>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k, vec,
-                    ds, (int)(pdl == 2), minhook, big);
+                    ds, (int)(pdl == 2), minhook, fb);
 }
 
 // --- VARIANT 5: per-CTA list of open edges ---------------------------------
@@ -374,11 +382,15 @@ static void update_deep_inst(const int* edges, int64_t k, int vec, int* parent, 
 template <int E>
 __global__ void __launch_bounds__(1024, 1)  // without the minimum, E = 1 and 2 were held to 32 registers and spilled
 k_update_tiles(int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
-               DevState* __restrict__ ds, int early, int minhook, const unsigned* __restrict__ big) {
+               DevState* __restrict__ ds, int early, int minhook, BigArgs fb) {
     extern __shared__ int4 open_list[];  // blockDim.x * E entries: (u, v, parent[u], parent[v])
     __shared__ unsigned n_open[2];
     pdl_trigger();
     if (!early) pdl_wait();
+    if (fb.alt && big_active(fb.big, ds)) {  // as in k_update
+        edges = fb.alt;
+        vec = pair_vec_dev(fb.alt);
+    }
     const int64_t T = (int64_t)blockDim.x * E;
     const int64_t tiles = (k + T - 1) / T;
     if (threadIdx.x == 0) n_open[0] = n_open[1] = 0u;
@@ -389,7 +401,7 @@ k_update_tiles(int* __restrict__ parent, int n, const int* __restrict__ edges, i
     int64_t e0 = t * T + (int64_t)threadIdx.x * E;
     if (t < tiles && e0 < k) load_pairs<E>(edges, e0, k, vec, u, v);
     if (early) pdl_wait();
-    const unsigned* bits = big_active(big, ds);
+    const unsigned* bits = big_active(fb.big, ds);
     if (t < tiles && e0 < k) m = edge_mask<E>(n, u, v, e0, k, ds, bits);
     gather_parents<E>(parent, m, u, v, pu, pv);
     __syncthreads();  // counters cleared
@@ -449,7 +461,7 @@ k_update_tiles(int* __restrict__ parent, int n, const int* __restrict__ edges, i
 
 template <int E>
 static void update_tiles_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds, int block,
-                              const cudaAccessPolicyWindow* window, int pdl, int minhook, const unsigned* big,
+                              const cudaAccessPolicyWindow* window, int pdl, int minhook, BigArgs fb,
                               cudaStream_t s) {
     const size_t smem = sizeof(int4) * (size_t)block * E;
     if (smem > 48 * 1024)  // the largest list (1024 threads x 4 edges) needs 64 KiB
@@ -462,7 +474,7 @@ static void update_tiles_inst(const int* edges, int64_t k, int vec, int* parent,
     const int64_t cap = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
     if (g > cap) g = cap;
     if (!window && !pdl) {
-        k_update_tiles<E><<<(unsigned)g, block, smem, s>>>(parent, n, edges, k, vec, ds, 0, minhook, big);
+        k_update_tiles<E><<<(unsigned)g, block, smem, s>>>(parent, n, edges, k, vec, ds, 0, minhook, fb);
         return;
     }
     cudaLaunchConfig_t cfg = {};
@@ -484,7 +496,7 @@ static void update_tiles_inst(const int* edges, int64_t k, int vec, int* parent,
     }
     cfg.attrs = attr;
     cfg.numAttrs = na;
-    cudaLaunchKernelEx(&cfg, k_update_tiles<E>, parent, n, edges, k, vec, ds, (int)(pdl == 2), minhook, big);
+    cudaLaunchKernelEx(&cfg, k_update_tiles<E>, parent, n, edges, k, vec, ds, (int)(pdl == 2), minhook, fb);
 }
 
 // --- VARIANT 4: filter pass + live-edge pass ------------------------------
@@ -504,15 +516,19 @@ template <int E>
 __global__ void __launch_bounds__(1024)
 k_update_filter(const int* __restrict__ parent, int n, const int* __restrict__ edges, int64_t k, int vec,
                 int4* __restrict__ live, unsigned* __restrict__ count, int sel, DevState* __restrict__ ds,
-                int early, const unsigned* __restrict__ big) {
+                int early, BigArgs fb) {
     pdl_trigger();
     if (!early) pdl_wait();
+    if (fb.alt && big_active(fb.big, ds)) {  // as in k_update
+        edges = fb.alt;
+        vec = pair_vec_dev(fb.alt);
+    }
     const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
     int u[E] = {}, v[E] = {};
     if (e0 < k) load_pairs<E>(edges, e0, k, vec, u, v);
     if (early) pdl_wait();
     if (blockIdx.x == 0 && threadIdx.x == 0) count[sel ^ 1] = 0u;
-    const unsigned m = e0 < k ? edge_mask<E>(n, u, v, e0, k, ds, big_active(big, ds)) : 0u;
+    const unsigned m = e0 < k ? edge_mask<E>(n, u, v, e0, k, ds, big_active(fb.big, ds)) : 0u;
     int pu[E], pv[E];
     gather_parents<E>(parent, m, u, v, pu, pv);
     unsigned open = 0;
@@ -564,11 +580,11 @@ k_update_live(int* __restrict__ parent, const int4* __restrict__ live, const uns
 template <int E>
 static void update_filter_inst(const int* edges, int64_t k, int vec, const int* parent, int n, int4* live,
                                unsigned* count, int sel, DevState* ds, int block,
-                               const cudaAccessPolicyWindow* window, int pdl, const unsigned* big,
+                               const cudaAccessPolicyWindow* window, int pdl, BigArgs fb,
                                cudaStream_t s) {
     const int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
     launch_windowed(k_update_filter<E>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k, vec,
-                    live, count, sel, ds, (int)(pdl == 2), big);
+                    live, count, sel, ds, (int)(pdl == 2), fb);
 }
 
 cudaError_t launch_update_split(int* parent, int n, const int* edges, int64_t k, DevState* ds, Launch cfg,
@@ -576,9 +592,9 @@ cudaError_t launch_update_split(int* parent, int n, const int* edges, int64_t k,
     if (k <= 0) return cudaSuccess;
     const int vec = pair_vec(edges);
     switch (cfg.ept) {
-        case 1: update_filter_inst<1>(edges, k, vec, parent, n, live, count, sel, ds, cfg.block, cfg.window, cfg.pdl, cfg.big, s); break;
-        case 2: update_filter_inst<2>(edges, k, vec, parent, n, live, count, sel, ds, cfg.block, cfg.window, cfg.pdl, cfg.big, s); break;
-        case 4: update_filter_inst<4>(edges, k, vec, parent, n, live, count, sel, ds, cfg.block, cfg.window, cfg.pdl, cfg.big, s); break;
+        case 1: update_filter_inst<1>(edges, k, vec, parent, n, live, count, sel, ds, cfg.block, cfg.window, cfg.pdl, BigArgs{cfg.big, cfg.alt}, s); break;
+        case 2: update_filter_inst<2>(edges, k, vec, parent, n, live, count, sel, ds, cfg.block, cfg.window, cfg.pdl, BigArgs{cfg.big, cfg.alt}, s); break;
+        case 4: update_filter_inst<4>(edges, k, vec, parent, n, live, count, sel, ds, cfg.block, cfg.window, cfg.pdl, BigArgs{cfg.big, cfg.alt}, s); break;
         default: return cudaErrorInvalidValue;
     }
     cudaError_t e = cudaGetLastError();
@@ -603,32 +619,32 @@ cudaError_t launch_update_split(int* parent, int n, const int* edges, int64_t k,
 template <int E, int VARIANT, bool WARP>
 static void update_inst2(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
                          int block, const cudaAccessPolicyWindow* window, int pdl, int minhook,
-                         const unsigned* big, cudaStream_t s) {
+                         BigArgs fb, cudaStream_t s) {
     int64_t g = (k + (int64_t)E * block - 1) / ((int64_t)E * block);
     if (VARIANT == 2) {
         const int64_t cap = resident_grid<k_update<E, VARIANT, WARP>>(block);
         if (g > cap) g = cap;
     }
     launch_windowed(k_update<E, VARIANT, WARP>, (unsigned)g, block, s, window, pdl != 0, parent, n, edges, k,
-                    vec, ds, (int)(pdl == 2), minhook, big);
+                    vec, ds, (int)(pdl == 2), minhook, fb);
 }
 
 // warphook applies to the lockstep variants (1, 2); variant 0 hooks per edge
 template <int E, int VARIANT>
 static void update_inst(const int* edges, int64_t k, int vec, int* parent, int n, DevState* ds,
                         int block, const cudaAccessPolicyWindow* window, int pdl, int minhook,
-                        int warphook, const unsigned* big, cudaStream_t s) {
+                        int warphook, BigArgs fb, cudaStream_t s) {
     if (VARIANT != 0 && warphook)
-        update_inst2<E, VARIANT, VARIANT != 0>(edges, k, vec, parent, n, ds, block, window, pdl, minhook, big, s);
+        update_inst2<E, VARIANT, VARIANT != 0>(edges, k, vec, parent, n, ds, block, window, pdl, minhook, fb, s);
     else
-        update_inst2<E, VARIANT, false>(edges, k, vec, parent, n, ds, block, window, pdl, minhook, big, s);
+        update_inst2<E, VARIANT, false>(edges, k, vec, parent, n, ds, block, window, pdl, minhook, fb, s);
 }
 
 cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevState* ds,
                           Launch cfg, cudaStream_t s) {
     if (k <= 0) return cudaSuccess;
     const int vec = pair_vec(edges);
-#define CC_UPD(E, V) update_inst<E, V>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, cfg.big, s)
+#define CC_UPD(E, V) update_inst<E, V>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, BigArgs{cfg.big, cfg.alt}, s)
     switch (cfg.variant * 8 + cfg.ept) {
         case 1: CC_UPD(1, 0); break;
         case 2: CC_UPD(2, 0); break;
@@ -639,12 +655,12 @@ cudaError_t launch_update(int* parent, int n, const int* edges, int64_t k, DevSt
         case 17: CC_UPD(1, 2); break;
         case 18: CC_UPD(2, 2); break;
         case 20: CC_UPD(4, 2); break;
-        case 25: update_deep_inst<1>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, cfg.big, s); break;
-        case 26: update_deep_inst<2>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, cfg.big, s); break;
-        case 28: update_deep_inst<4>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, cfg.big, s); break;
-        case 41: update_tiles_inst<1>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.big, s); break;
-        case 42: update_tiles_inst<2>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.big, s); break;
-        case 44: update_tiles_inst<4>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.big, s); break;
+        case 25: update_deep_inst<1>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, BigArgs{cfg.big, cfg.alt}, s); break;
+        case 26: update_deep_inst<2>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, BigArgs{cfg.big, cfg.alt}, s); break;
+        case 28: update_deep_inst<4>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, cfg.warphook, BigArgs{cfg.big, cfg.alt}, s); break;
+        case 41: update_tiles_inst<1>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, BigArgs{cfg.big, cfg.alt}, s); break;
+        case 42: update_tiles_inst<2>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, BigArgs{cfg.big, cfg.alt}, s); break;
+        case 44: update_tiles_inst<4>(edges, k, vec, parent, n, ds, cfg.block, cfg.window, cfg.pdl, cfg.minhook, BigArgs{cfg.big, cfg.alt}, s); break;
         default: return cudaErrorInvalidValue;
     }
 #undef CC_UPD

@@ -88,9 +88,13 @@ __device__ __forceinline__ int block_exclusive_scan(int* a, int nb, int* warp_su
 // it still see everything before it complete.
 __global__ void __launch_bounds__(kOrderBlock)
 k_order_count(const int* __restrict__ edges, int64_t k, int vec, int n, int shift, int nb,
-              int* __restrict__ totals, int early) {
+              int* __restrict__ totals, int early, const unsigned* big, const DevState* ds) {
     __shared__ int hist[kMaxBuckets];
     pdl_trigger_o();
+    if (big && ds->big_root >= 0) {  // the update reads the caller's order (BigArgs)
+        pdl_wait_o();                // still complete only after the kernel before
+        return;
+    }
     if (!early) pdl_wait_o();
     for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
     __syncthreads();
@@ -113,7 +117,7 @@ k_order_count(const int* __restrict__ edges, int64_t k, int vec, int n, int shif
 __global__ void __launch_bounds__(kOrderBlock)
 k_order_scatter(const int* __restrict__ edges, int64_t k, int vec, int n, int shift, int nb,
                 int* __restrict__ totals, int* __restrict__ fill, unsigned* __restrict__ done,
-                int2* __restrict__ out) {
+                int2* __restrict__ out, const unsigned* big, const DevState* ds) {
     __shared__ int start[kMaxBuckets];   // global first slot of each bucket
     __shared__ int cnt[kMaxBuckets];     // this tile: edges per bucket, then their local starts
     __shared__ int gbase[kMaxBuckets];   // this tile: global slot of its first edge of each bucket
@@ -123,6 +127,7 @@ k_order_scatter(const int* __restrict__ edges, int64_t k, int vec, int n, int sh
     __shared__ bool last;
     pdl_trigger_o();
     pdl_wait_o();  // totals are complete
+    if (big && ds->big_root >= 0) return;  // as in k_order_count: nothing was counted
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         start[b] = totals[b];
         cnt[b] = 0;
@@ -226,7 +231,8 @@ int order_shift(int64_t n, int log_buckets) {
 int64_t order_counter_ints(int log_buckets) { return 2 * ((int64_t)1 << log_buckets) + 1; }
 
 cudaError_t launch_order_edges(const int* edges, int64_t k, int n, int log_buckets, int* counters,
-                               int* out, int pdl, cudaStream_t s, int* kernels) {
+                               int* out, int pdl, cudaStream_t s, int* kernels, const unsigned* big,
+                               const DevState* ds) {
     *kernels = 0;
     if (k <= 0) return cudaSuccess;
     if (log_buckets < 0 || (1 << log_buckets) > kMaxBuckets) return cudaErrorInvalidValue;
@@ -241,10 +247,10 @@ cudaError_t launch_order_edges(const int* edges, int64_t k, int n, int log_bucke
     // edges before the wait (pdl 2): launched early just to wait, its CTAs
     // would hold SM slots that the previous kernel's remaining CTAs need.
     cudaError_t e = launch_pdl(k_order_count, (unsigned)G, s, pdl == 2, edges, k, vec, n, shift, nb, totals,
-                               (int)(pdl == 2));
+                               (int)(pdl == 2), big, ds);
     if (e != cudaSuccess) return e;
     e = launch_pdl(k_order_scatter, (unsigned)G, s, pdl != 0, edges, k, vec, n, shift, nb, totals, fill, done,
-                   reinterpret_cast<int2*>(out));
+                   reinterpret_cast<int2*>(out), big, ds);
     *kernels = 2;
     return e;
 }

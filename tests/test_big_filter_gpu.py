@@ -182,3 +182,29 @@ def test_segmented_handle_rejects_the_filter(cc):
     assert ex.value.status == cc.CC_ERR_UNSUPPORTED
     assert f.get_option("big_filter") == 0
     f.close()
+
+
+@pytest.mark.parametrize("offset", [0, 1, 2], ids=["16B", "4B", "8B"])
+def test_ordered_update_reads_the_callers_edges_while_the_filter_is_on(cc, offset):
+    # edge order + filter: once the bitmap marks a tree, the order kernels do
+    # nothing and the update reads the caller's array, here starting 0, 4 or 8
+    # bytes past a 16-byte boundary; compared with the oracle after every
+    # minibatch of a 512 x 512 grid stream, through the point where the filter
+    # turns on
+    s = I.grid_stream(512, 512, batch=(1 << 14) + 1, q=1 << 13, seed=5)
+    f = cc.Forest(s.n, big_filter=128, edge_order=7, compress_every=2, update_variant=5, block=128)
+    ref = oracle.OracleUF(s.n)
+    on = 0
+    for i, (e, q) in enumerate(s):
+        buf = torch.empty(2 * len(e) + 4, dtype=torch.int32, device="cuda")
+        view = buf[offset:offset + 2 * len(e)].view(-1, 2)
+        view.copy_(dev(e))
+        f.bulk_update(view)
+        ref.bulk_update(e)
+        got = f.bulk_query(dev(q)).cpu().numpy()
+        assert np.array_equal(got, ref.bulk_query(q)), f"answers differ at minibatch {i}"
+        on += f.big_filter_stats()[0] >= 0
+    assert on >= 4, "the filter never turned on"
+    assert np.array_equal(f.labels().cpu().numpy(), ref.labels())
+    assert f.kernel_stats()["order"] == 2 * s.batches
+    f.sync()

@@ -107,6 +107,15 @@ OPTION_SETS = {
     "big_warp_query": {"big_filter": 1, "query_variant": 2, "compress_every": 1},
     "big_all_samples": {"big_filter": 1024, "compress_every": 1},
     "big_touched_scope_never_built": {"big_filter": 1, "compress_scope": 1},
+    # with the edge order: the order is skipped and the caller's edges read while the bitmap is in use
+    "big_ordered_lockstep_every1": {"big_filter": 1, "edge_order": 6, "update_variant": 1, "compress_every": 1},
+    "big_ordered_two_pass": {"big_filter": 1, "edge_order": 9, "update_variant": 4, "compress_every": 2},
+    "big_ordered_deep_pdl2": {"big_filter": 1, "edge_order": 8, "update_variant": 3, "edges_per_thread": 2,
+                              "pdl": 2, "compress_every": 2},
+    "big_ordered_persistent_ept1": {"big_filter": 64, "edge_order": 7, "update_variant": 2, "edges_per_thread": 1,
+                                    "block": 512, "compress_every": 3, "pdl": 2},
+    "big_ordered_paper_schedule": {"big_filter": 1, "edge_order": 8, "update_schedule": 1, "compress_every": 2},
+    "big_ordered_touched_scope": {"big_filter": 1, "edge_order": 7, "compress_scope": 1, "compress_every": 2},
 }
 
 
@@ -172,7 +181,8 @@ def test_uniform_small_every_batch(cc, opts):
                                   "cta_list_ept2_min", "cta_list_ept4_b1024",
                                   "warp_query_halving_ignored_pdl2", "big_default", "big_every1_flat_query",
                                   "big_cta_list_ordered_min", "big_persistent_query_halving", "big_deep_pdl2",
-                                  "big_two_pass", "big_lockstep_warp_hook"])
+                                  "big_two_pass", "big_lockstep_warp_hook", "big_ordered_two_pass",
+                                  "big_ordered_paper_schedule"])
 def test_rmat_small(cc, opts):
     s = I.rmat_stream(scale=16, m=1 << 20, batch=(1 << 16) + 3, q=(1 << 16) - 5, seed=1)
     run_stream(cc, s, OPTION_SETS[opts], label_every=4, check_invariants=True)
@@ -186,7 +196,9 @@ def test_rmat_small(cc, opts):
                                   "warp_query", "warp_query_flat_b1024", "cta_list_ept1_b128", "cta_list_ordered",
                                   "big_default", "big_every1_flat_query", "big_cta_list_ordered_min",
                                   "big_cta_list_ept1", "big_splitting_query", "big_per_edge_query_ept4",
-                                  "big_warp_query", "big_all_samples"])
+                                  "big_warp_query", "big_all_samples", "big_ordered_lockstep_every1",
+                                  "big_ordered_two_pass", "big_ordered_deep_pdl2", "big_ordered_persistent_ept1",
+                                  "big_ordered_paper_schedule", "big_ordered_touched_scope"])
 def test_grid_small(cc, opts):
     s = I.grid_stream(512, 512, batch=(1 << 14) + 1, q=1 << 14, seed=2)
     ref = run_stream(cc, s, OPTION_SETS[opts], label_every=8, check_invariants=True)
