@@ -55,3 +55,19 @@ def test_default_bench_line():
     assert sv["saturation"]["edges_per_s"] > 0 and len(sv["saturation"]["runs_edges_per_s"]) == 3
     assert set(sv["latency_at_load"]) == {"0.5", "0.8", "0.95"}
     assert sv["served_labels_equal_plain"] is True
+
+
+def test_stream_runner_for_profilers():
+    # the command the ncu summaries name: a few minibatches with the tuned
+    # options, and with an option given over them
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    for extra in ([], ["--opt", "big_filter=0", "--opt", "compress_every=4"]):
+        r = subprocess.run([sys.executable, "-m", "paper_1602_05232_gb300.stream_run", "--workload", "rmat",
+                            "--minibatches", "3", *extra],
+                           cwd=ROOT, capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        assert "rmat: 3 minibatches" in r.stdout
+    r = subprocess.run([sys.executable, "-m", "paper_1602_05232_gb300.stream_run", "--opt", "no_such=1"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0 and "unknown option" in r.stderr
