@@ -545,6 +545,29 @@ def test_paper_scale_random_stream_component_curve(cc):
     f.sync()
 
 
+def test_paper_scale_3dgrid_stream_component_curve(cc):
+    # the 464^3 mesh (99.9 M vertices, 299 M edges) in minibatches of 10^7 at
+    # its tuned options: edge order, update variant 5, the largest-component
+    # filter, which turns the order off once it marks a tree. Component count
+    # after every minibatch and the final labels against the oracle
+    from bench import launch_options
+    s = I.paper_stream("3dgrid", batch=10_000_000, q=1)
+    opts = launch_options("paper-3dgrid")
+    f = cc.Forest(s.n, **opts)
+    ref = oracle.OracleUF(s.n)
+    on = 0
+    for i in range(s.batches):
+        e = s.edges(i)
+        f.bulk_update(dev(e))
+        ref.bulk_update(e)
+        assert f.components() == ref.components, f"component count at minibatch {i}"
+        on += opts.get("big_filter", 0) > 0 and f.big_filter_stats()[0] >= 0
+    assert np.array_equal(f.labels().cpu().numpy(), ref.labels())
+    if opts.get("big_filter", 0) > 0:
+        assert on > 0, "the filter never turned on"
+    f.sync()
+
+
 def test_single_vertex_forest(cc):
     f = cc.Forest(1)
     f.bulk_update(dev(np.array([[0, 0]], dtype=np.int32)))
