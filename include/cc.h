@@ -164,7 +164,8 @@ typedef enum {
                                     instead of once per endpoint. The scratch (8 B per edge of the
                                     largest minibatch so far, plus 8 B per bucket) is allocated on
                                     first use and grown with one stream synchronisation. Counted
-                                    as CC_K_ORDER launches (two per ordered minibatch) */
+                                    as CC_K_ORDER launches (two per ordered minibatch; they return
+                                    at once while CC_OPT_BIG_FILTER's bitmap is in use) */
     CC_OPT_HOOK_WARP = 22,       /* 1 = the fused Bulk-Update's lockstep variants (CC_OPT_UPDATE_VARIANT
                                     1..4) group the hooks of a warp by target root: one lane per
                                     distinct target writes it (compare-and-swap or atomicMin, per
@@ -184,7 +185,10 @@ typedef enum {
                                     stay connected: the fused Bulk-Query (CC_OPT_QUERY_VARIANT 0, 1)
                                     answers a pair of marked vertices with 1 without reading the
                                     forest, and the fused Bulk-Update drops an edge between marked
-                                    vertices before its parent reads. cc_reset, cc_load_labels and
+                                    vertices before its parent reads. While it is in use, the edge
+                                    order (CC_OPT_EDGE_ORDER) of the fused update does nothing and
+                                    the update reads the caller's edges; this is decided on the
+                                    device, with no synchronisation. cc_reset, cc_load_labels and
                                     cc_load_forest turn it off until the next pass. Plain handles,
                                     default link rule; CC_ERR_UNSUPPORTED on a segmented handle.
                                     Same answers and labels. Pick launches count as CC_K_BIG_PICK */
