@@ -766,6 +766,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int, dist, workload: str | 
     gpu_launches = sum(la1[k] - la0[k] for k in la1)
     depth_max, depth_mean = f.depth()
     f.sync()
+    expect = d_out.cpu() if e2e else None       # the last pass's answers, for the e2e check
     gather = gather_ceiling(f, views)
 
     total_ms_max = dist_max(dist, total_ms, dev)
@@ -824,7 +825,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int, dist, workload: str | 
 
     upd_ms = sum(kstats[k][1] for k in ("update", "compress_all", "compress_touched"))
     qry_ms = kstats["query"][1]
-    e2e_out = run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist, workload, K, W) if e2e else None
+    e2e_out = run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist, workload, K, W, expect) if e2e else None
 
     f.close()
     del views, d_edges, d_pairs, d_out
@@ -909,7 +910,8 @@ def gather_ceiling(f, views, reps: int = 20) -> dict | None:
                     "practical ceiling of this access pattern on this GPU, beside the copy-bandwidth peak"}
 
 
-def run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist, workload: str, K: int, W: int) -> dict:
+def run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist, workload: str, K: int, W: int,
+            expect=None) -> dict:
     """Same metric through the public API from HOST buffers (pinned), with the
     host<->device traffic of every pass inside the timed region: each pass
     resets the forest, and its edges and pairs go to the device and its
@@ -919,9 +921,12 @@ def run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist, workload: str, K: 
                  link (NVLink-C2C on Grace-Blackwell);
       pipelined  the inputs are copied to device buffers on a copy stream,
                  G consecutive minibatches per copy (two buffers, the next
-                 group's copy overlapping this group's kernels), and the
-                 answers copied back, G = 1, 2, 4.
-    The better of the two is the e2e value; both are reported."""
+                 group's copy overlapping this group's kernels, also across
+                 the boundary between two passes), and the answers copied
+                 back, G = 1, 2, 4.
+    The better of the two is the e2e value; both are reported. Each way's
+    answers of its last pass are compared with `expect` (the device-resident
+    run's), and a difference is an error."""
     import torch
     from paper_1602_05232_gb300 import cc
 
@@ -938,18 +943,29 @@ def run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist, workload: str, K: 
             f = cc.Forest(s.n, stream=stream, **opts)
             for _ in range(max(1, min(W, 2))):
                 run_pass(f)
+            if getattr(run_pass, "finish", None):
+                run_pass.finish()
             stream.synchronize()
             dist_barrier(dist)
             a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             for _ in range(K):
                 run_pass(f)
+            finish = getattr(run_pass, "finish", None)
+            if finish:
+                finish()                          # the last answers are on the host
             b_.record(stream)
             stream.synchronize()
             dist_barrier(dist)
             f.sync()
             f.close()
         return dist_max(dist, a.elapsed_time(b_), dev)
+
+    def check(name: str) -> None:
+        if expect is not None and not torch.equal(h_o, expect):
+            bad = int((h_o != expect).sum())
+            raise RuntimeError(f"e2e {name}: {bad} answers differ from the device-resident run")
+        h_o.zero_()
 
     zero_copy_ok = cc.device_can_read(h_edges) and cc.device_can_read(h_o)
     if zero_copy_ok:
@@ -962,6 +978,7 @@ def run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist, workload: str, K: 
                 f.bulk_update(e)
                 f.bulk_query(q, out=o)
         results["zero_copy"] = timed(zc)
+        check("zero_copy")
 
     copy_in = torch.cuda.Stream(device=dev)
     copy_out = torch.cuda.Stream(device=dev)
@@ -994,10 +1011,17 @@ def run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist, workload: str, K: 
         done_ev = [torch.cuda.Event(), torch.cuda.Event()]
         ready_ev = [torch.cuda.Event(), torch.cuda.Event()]
         out_ev = [torch.cuda.Event(), torch.cuda.Event()]
+        started = [False]
 
         def piped(f):
-            for e in done_ev + out_ev:
-                e.record(stream)
+            # Buffer j's events carry over from the previous pass: the first
+            # copy of this pass waits only for that buffer's last kernels, so it
+            # overlaps the previous pass's last group (its answers still come
+            # back before the kernels that reuse the buffer).
+            if not started[0]:
+                for e in done_ev + out_ev:
+                    e.record(stream)
+                started[0] = True
 
             def issue_copy(gi):
                 j, he, de, hq, dq = plan[gi][:5]
@@ -1022,12 +1046,17 @@ def run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist, workload: str, K: 
                 with torch.cuda.stream(copy_out):
                     ho.copy_(do, non_blocking=True)
                 out_ev[j].record(copy_out)
+
+        def finish():
             stream.wait_event(out_ev[0])
             stream.wait_event(out_ev[1])
+
+        piped.finish = finish
         return piped
 
     for G in (1, 2, 4):
         results[f"pipelined_g{G}"] = timed(make_piped(G))
+        check(f"pipelined_g{G}")
     edges_all = dist_sum(dist, float(K * s.m), dev)
     best = min(results, key=results.get)
     return {"value": round(edges_all / (results[best] / 1e3), 1), "unit": "edges/s",
@@ -1036,8 +1065,11 @@ def run_e2e(args, s, h_edges, h_pairs, eoff, qoff, dev, dist, workload: str, K: 
             "variants": {k: round(edges_all / (v / 1e3), 1) for k, v in results.items()},
             "what": "pinned host buffers through cc_bulk_update/cc_bulk_query, one whole pass per "
                     "step; zero_copy: the kernels read/write host memory directly; pipelined_gG: "
-                    "copies on two copy streams overlapping the kernels, G minibatches per copy "
-                    "(one update and one query call per minibatch)"}
+                    "copies on two copy streams overlapping the kernels (and the next pass's first "
+                    "copy overlapping this pass's last kernels), G minibatches per copy (one update "
+                    "and one query call per minibatch); every way's answers equal the device-resident "
+                    "run's",
+            "answers_checked": expect is not None}
 
 
 # ------------------------------------------------------------ CPU oracle
