@@ -343,18 +343,25 @@ cc_status cc_submit(cc_ctx* ctx, const cc_op* ops, int64_t nops);
  *  - A group of queries runs as ONE Bulk-Query launch.
  * The stages overlap on the device:
  *  - Request data is copied from host memory into a device staging ring on a
- *    copy stream while earlier groups compute.
+ *    copy stream while earlier groups compute. Updates and queries have a
+ *    ring each, and requests whose host data follow one another (as in one
+ *    caller buffer) and land next to each other in their ring share one
+ *    copy, across the groups the worker forms at a time (up to 64), so the
+ *    copies stay large when the groups are small.
  *  - Query answers go back on a second copy stream.
  *  - Groups compute in arrival order on one compute stream, so no query
  *    overlaps a later update.
- * A request is admitted when its footprint (8 bytes in + 1 byte out per
- * pair) fits in the free part of the ring; otherwise it waits for earlier
- * groups to finish. Latency runs from enqueue to the moment a completion
+ * A request is admitted when its footprint (8 bytes in, plus 1 byte out per
+ * query pair) fits in the free part of its kind's ring; otherwise it waits for
+ * earlier groups to finish. Latency runs from enqueue to the moment a completion
  * thread sees the event recorded after the group's last device operation. */
 typedef struct cc_server cc_server;
 
 typedef struct {
-    int64_t ring_pairs;       /* staging capacity in pairs (<= 0: 2^25, i.e. 288 MiB) */
+    int64_t ring_pairs;       /* staging capacity in pairs of EACH of the two device rings, one for
+                                 update edges and one for query pairs (<= 0: 2^25, i.e. 256 MiB
+                                 each, plus 32 MiB of query answers); also the largest k a
+                                 request may have */
     int64_t max_group_pairs;  /* most pairs merged into one launch (<= 0: 2^22) */
     int32_t merge;            /* 1: merge consecutive same-kind requests (default); 0: one launch per request */
 } cc_server_config;

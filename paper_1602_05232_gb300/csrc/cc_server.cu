@@ -5,13 +5,19 @@
 //  - callers enqueue requests (any thread); each gets a ticket and an arrival
 //    time;
 //  - one worker thread cuts the arrived, not yet launched requests into
-//    groups of consecutive same-kind requests, reserves a contiguous range of
-//    the device staging ring for each group, copies the group's host data in
-//    on the h2d stream, and launches ONE Bulk-Update or Bulk-Query over the
-//    range on the compute stream (after the copy). Query answers go back on
-//    the d2h stream. An event recorded after the group's last operation is
-//    watched by a completion thread, which stamps the completion time and
-//    frees the group's ring range;
+//    groups of consecutive same-kind requests (up to kMaxBatch groups at a
+//    time), reserves a contiguous range of its kind's device staging ring for
+//    each group (one ring for update edges, one for query pairs), copies the
+//    host data in on the h2d stream, and launches ONE Bulk-Update or
+//    Bulk-Query per group over its range on the compute stream, after the
+//    copy that carried its data. Requests whose host data follow one another
+//    and land next to each other in their ring share one copy, also across
+//    groups: with the two kinds in separate rings, the update groups of a
+//    batch that alternates updates and queries still fill one run of the
+//    update ring, so the copies stay large when the groups are small. Query
+//    answers go back on the d2h stream. An event recorded after the group's
+//    last operation is watched by a completion thread, which stamps the
+//    completion time and frees the group's ring range;
 //  - groups compute in arrival order on the single compute stream, so a
 //    query sees exactly the updates that arrived before it. Merging adjacent
 //    updates is exact because the graph is the union of the edge sets.
@@ -53,11 +59,22 @@ struct Req {
 struct Group {
     cc_server* srv;
     int64_t first, last;  // requests [first, last)
+    int32_t kind;         // CC_OP_UPDATE or CC_OP_QUERY: which ring
     int64_t b, e;         // ring range [b, e) in pairs
     cudaEvent_t ev = nullptr;  // recorded after the group's last operation
     bool launched = false;     // ev has been recorded
     bool done = false;
 };
+
+// A staging ring of pairs on the device: FIFO ranges, see ring_alloc.
+struct Ring {
+    int32_t* buf = nullptr;  // 2 * cap ints
+    int64_t head = 0;
+    int64_t used = 0;        // pairs held by in-flight groups of this ring's kind
+};
+
+constexpr int kMaxBatch = 64;                     // groups formed per pass of the worker
+constexpr int64_t kMaxRunPairs = (int64_t)1 << 22;  // 32 MiB: a longer copy run only delays its first group
 
 }  // namespace
 
@@ -66,10 +83,11 @@ struct cc_server {
     cudaStream_t prev_stream = nullptr;
     int device = 0;
     cudaStream_t compute = nullptr, h2d = nullptr, d2h = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_q = nullptr;
-    int32_t* ring = nullptr;
-    uint8_t* ring_out = nullptr;
-    int64_t cap = 0, max_group = 0;
+    cudaEvent_t ev_q = nullptr;
+    std::vector<cudaEvent_t> run_ev;   // one per copy run of a batch (worker thread only)
+    Ring ring[2];                      // [CC_OP_UPDATE], [CC_OP_QUERY]
+    uint8_t* ring_out = nullptr;       // query answers, at the query ring's offsets
+    int64_t cap = 0, max_group = 0;    // cap: pairs per ring
     bool merge = true;
 
     std::mutex mu;
@@ -81,8 +99,6 @@ struct cc_server {
     std::deque<Req> reqs;
     int64_t next_launch = 0, completed = 0, groups = 0;
     int64_t n_upd = 0, n_qry = 0, edges = 0, pairs = 0;
-    int64_t head = 0;
-    int64_t used = 0;  // ring pairs held by in-flight groups
     std::deque<Group*> inflight;
     bool stop = false;
     cc_status err = CC_OK;
@@ -116,7 +132,7 @@ void mark_done(cc_server* s, Group* g, double t) {
     g->done = true;
     while (!s->inflight.empty() && s->inflight.front()->done) {
         Group* f = s->inflight.front();
-        s->used -= f->e - f->b;
+        s->ring[f->kind].used -= f->e - f->b;
         s->spare_events.push_back(f->ev);
         delete f;
         s->inflight.pop_front();
@@ -169,153 +185,212 @@ void reaper_loop(cc_server* s) {
     }
 }
 
-// Reserve [b, b+k) of the ring (FIFO). Called with the lock held.
+// Reserve [b, b+k) of the ring of `kind` (FIFO). Called with the lock held.
 //
-// Groups take ranges in launch order and free them in the same order, so the
-// occupied part is one arc from the oldest non-empty in-flight group's start
-// (tail) to head, possibly wrapping past the end. Emptiness is decided by the
-// number of pairs held, not by head == tail: a group of zero pairs sits at
-// head without occupying anything, and when it is the oldest in flight while
-// later groups have filled the ring all the way round, head == tail means
-// full.
-bool ring_alloc(cc_server* s, int64_t k, int64_t* b) {
-    if (s->used == 0) s->head = 0;
+// Groups of a kind take ranges of its ring in launch order and free them in
+// the same order, so the occupied part is one arc from the oldest non-empty
+// in-flight group's start (tail) to head, possibly wrapping past the end.
+// Emptiness is decided by the number of pairs held, not by head == tail: a
+// group of zero pairs sits at head without occupying anything, and when it is
+// the oldest in flight while later groups have filled the ring all the way
+// round, head == tail means full.
+bool ring_alloc(cc_server* s, int32_t kind, int64_t k, int64_t* b) {
+    Ring& r = s->ring[kind];
+    if (r.used == 0) r.head = 0;
     if (k == 0) {
-        *b = s->head;
+        *b = r.head;
         return true;
     }
-    if (s->used == 0) {
+    if (r.used == 0) {
         if (k > s->cap) return false;
         *b = 0;
         return true;
     }
-    int64_t tail = s->head;
+    int64_t tail = r.head;
     for (const Group* g : s->inflight)
-        if (g->e > g->b) {
+        if (g->kind == kind && g->e > g->b) {
             tail = g->b;
             break;
         }
-    if (s->head > tail) {
+    if (r.head > tail) {
         // occupied [tail, head): free space at the end, then at the start
-        if (s->cap - s->head >= k) { *b = s->head; return true; }
+        if (s->cap - r.head >= k) { *b = r.head; return true; }
         if (tail >= k) { *b = 0; return true; }
         return false;
     }
     // wrapped: occupied [tail, cap) and [0, head); free [head, tail)
-    if (tail - s->head >= k) { *b = s->head; return true; }
+    if (tail - r.head >= k) { *b = r.head; return true; }
     return false;
 }
 
 
+// One group of a batch, as the worker's device-work section sees it.
+struct Planned {
+    Group* g;
+    int64_t r0, r1;  // its requests: batch[r0, r1)
+    int need;        // the last copy run that carries its data, or -1
+};
+
+// A copy of host data that follow one another into consecutive ring slots.
+struct Run {
+    int32_t kind;
+    const int32_t* src;
+    int64_t dst, pairs;   // ring offset and length, in pairs
+    int64_t r0, r1;       // the batch requests it covers
+};
+
 void worker_loop(cc_server* s) {
     cudaSetDevice(s->device);
     std::vector<Req> batch;
+    std::vector<Planned> plan;
+    std::vector<Run> runs;
+    std::vector<int> run_of;  // batch request -> run, or -1 (empty request)
     for (;;) {
-        int64_t first, last, b = 0, total = 0;
-        int32_t kind;
-        Group* g = nullptr;
+        plan.clear();
+        batch.clear();
         {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv_work.wait(lk, [&] { return s->stop || s->err != CC_OK || s->next_launch < (int64_t)s->reqs.size(); });
             if (s->err != CC_OK) return;
             if (s->next_launch >= (int64_t)s->reqs.size()) return;  // stop, nothing left
-            for (;;) {
+            while ((int)plan.size() < kMaxBatch && s->next_launch < (int64_t)s->reqs.size()) {
                 // the longest run of same-kind requests that fits one launch
-                first = s->next_launch;
-                kind = s->reqs[first].kind;
-                last = first;
-                total = 0;
+                const int64_t first = s->next_launch;
+                const int32_t kind = s->reqs[first].kind;
+                int64_t last = first, total = 0, b = 0;
                 while (last < (int64_t)s->reqs.size() && s->reqs[last].kind == kind &&
                        (last == first || (s->merge && total + s->reqs[last].k <= s->max_group))) {
                     total += s->reqs[last].k;
                     last++;
                 }
-                // shrink it until its staging range fits; else wait for room
-                while (!ring_alloc(s, total, &b) && last - first > 1) total -= s->reqs[--last].k;
-                if (ring_alloc(s, total, &b)) break;
-                s->cv_work.wait(lk);
-                if (s->err != CC_OK) return;
-            }
-            g = new Group{s, first, last, b, b + total};
-            if (!s->spare_events.empty()) {
-                g->ev = s->spare_events.back();
-                s->spare_events.pop_back();
-            }
-            s->inflight.push_back(g);
-            s->head = b + total;
-            s->used += total;
-            s->next_launch = last;
-            s->groups++;
-            batch.clear();
-            int64_t off = b;
-            for (int64_t i = first; i < last; i++) {
-                s->reqs[i].off = off;
-                off += s->reqs[i].k;
-                batch.push_back(s->reqs[i]);
+                // shrink it until its staging range fits; else launch what the
+                // batch has, or wait for room
+                while (!ring_alloc(s, kind, total, &b) && last - first > 1) total -= s->reqs[--last].k;
+                if (!ring_alloc(s, kind, total, &b)) {
+                    if (!plan.empty()) break;
+                    s->cv_work.wait(lk);
+                    if (s->err != CC_OK) return;
+                    continue;
+                }
+                Group* g = new Group{s, first, last, kind, b, b + total};
+                if (!s->spare_events.empty()) {
+                    g->ev = s->spare_events.back();
+                    s->spare_events.pop_back();
+                }
+                s->inflight.push_back(g);
+                s->ring[kind].head = b + total;
+                s->ring[kind].used += total;
+                s->next_launch = last;
+                s->groups++;
+                const int64_t r0 = (int64_t)batch.size();
+                int64_t off = b;
+                for (int64_t i = first; i < last; i++) {
+                    s->reqs[i].off = off;
+                    off += s->reqs[i].k;
+                    batch.push_back(s->reqs[i]);
+                }
+                plan.push_back({g, r0, (int64_t)batch.size(), -1});
             }
         }
-        // --- device work for the group (no lock held) ---
+        // --- device work for the batch (no lock held) ---
         cudaError_t e = cudaSuccess;
-        if (!g->ev) e = cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming);
-        // copy in: one copy per run of requests whose host data is contiguous;
-        // if the driver refuses a run (it spans two separate host
-        // allocations), copy its requests one by one
-        for (size_t i = 0; i < batch.size() && e == cudaSuccess;) {
-            size_t j = i + 1;
-            int64_t pairs = batch[i].k;
-            while (j < batch.size() && batch[j].data == batch[i].data + 2 * pairs) pairs += batch[j++].k;
-            if (pairs > 0) {
-                e = cudaMemcpyAsync(s->ring + 2 * batch[i].off, batch[i].data, sizeof(int32_t) * 2 * (size_t)pairs,
-                                    cudaMemcpyHostToDevice, s->h2d);
-                if (e == cudaErrorInvalidValue && j > i + 1) {
-                    cudaGetLastError();
-                    e = cudaSuccess;
-                    for (size_t r = i; r < j && e == cudaSuccess; r++)
-                        if (batch[r].k > 0)
-                            e = cudaMemcpyAsync(s->ring + 2 * batch[r].off, batch[r].data,
-                                                sizeof(int32_t) * 2 * (size_t)batch[r].k, cudaMemcpyHostToDevice, s->h2d);
+        for (Planned& p : plan)
+            if (!p.g->ev && e == cudaSuccess) e = cudaEventCreateWithFlags(&p.g->ev, cudaEventDisableTiming);
+        // copy runs: a request extends the open run of its kind when its host
+        // data and its ring slots both follow on; runs are numbered in the
+        // order of their first request, which is the order they are copied
+        runs.clear();
+        run_of.assign(batch.size(), -1);
+        int open[2] = {-1, -1};
+        for (Planned& p : plan) {
+            const int32_t kind = p.g->kind;
+            for (int64_t i = p.r0; i < p.r1; i++) {
+                const Req& r = batch[i];
+                if (r.k == 0) continue;
+                int o = open[kind];
+                if (o >= 0 && runs[o].src + 2 * runs[o].pairs == r.data && runs[o].dst + runs[o].pairs == r.off &&
+                    runs[o].pairs + r.k <= kMaxRunPairs) {
+                    runs[o].pairs += r.k;
+                    runs[o].r1 = i + 1;
+                } else {
+                    runs.push_back({kind, r.data, r.off, r.k, i, i + 1});
+                    o = open[kind] = (int)runs.size() - 1;
                 }
+                run_of[i] = o;
+                if (o > p.need) p.need = o;
             }
-            i = j;
         }
-        if (e == cudaSuccess) e = cudaEventRecord(s->ev_in, s->h2d);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s->compute, s->ev_in, 0);
-        if (e != cudaSuccess) { fail_worker(s, e, "serve: staging copy"); return; }
-        if (kind == CC_OP_UPDATE) {
-            cc_status st = total ? cc_bulk_update(s->ctx, s->ring + 2 * b, total) : CC_OK;
-            if (st != CC_OK) { fail_worker(s, cudaErrorUnknown, "serve: bulk update"); return; }
-            e = cudaEventRecord(g->ev, s->compute);
-        } else {
-            cc_status st = total ? cc_bulk_query(s->ctx, s->ring + 2 * b, total, s->ring_out + b) : CC_OK;
-            if (st != CC_OK) { fail_worker(s, cudaErrorUnknown, "serve: bulk query"); return; }
-            e = cudaEventRecord(s->ev_q, s->compute);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->d2h, s->ev_q, 0);
-            for (size_t i = 0; i < batch.size() && e == cudaSuccess;) {  // contiguous outputs: one copy
-                size_t j = i + 1;
-                int64_t pairs = batch[i].k;
-                while (j < batch.size() && batch[j].out == batch[i].out + pairs) pairs += batch[j++].k;
-                if (pairs > 0) {
-                    e = cudaMemcpyAsync(batch[i].out, s->ring_out + batch[i].off, (size_t)pairs,
-                                        cudaMemcpyDeviceToHost, s->d2h);
-                    if (e == cudaErrorInvalidValue && j > i + 1) {  // spans two allocations
-                        cudaGetLastError();
-                        e = cudaSuccess;
-                        for (size_t r = i; r < j && e == cudaSuccess; r++)
-                            if (batch[r].k > 0)
-                                e = cudaMemcpyAsync(batch[r].out, s->ring_out + batch[r].off, (size_t)batch[r].k,
-                                                    cudaMemcpyDeviceToHost, s->d2h);
-                    }
-                }
-                i = j;
+        while (s->run_ev.size() < runs.size() && e == cudaSuccess) {
+            cudaEvent_t ev = nullptr;
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) s->run_ev.push_back(ev);
+        }
+        // copy in, run by run; if the driver refuses a run (it spans two
+        // separate host allocations), copy its requests one by one
+        for (size_t ri = 0; ri < runs.size() && e == cudaSuccess; ri++) {
+            const Run& r = runs[ri];
+            int32_t* dst = s->ring[r.kind].buf + 2 * r.dst;
+            e = cudaMemcpyAsync(dst, r.src, sizeof(int32_t) * 2 * (size_t)r.pairs, cudaMemcpyHostToDevice, s->h2d);
+            if (e == cudaErrorInvalidValue && r.r1 - r.r0 > 1) {
+                cudaGetLastError();
+                e = cudaSuccess;
+                for (int64_t i = r.r0; i < r.r1 && e == cudaSuccess; i++)
+                    if (run_of[i] == (int)ri)
+                        e = cudaMemcpyAsync(s->ring[r.kind].buf + 2 * batch[i].off, batch[i].data,
+                                            sizeof(int32_t) * 2 * (size_t)batch[i].k, cudaMemcpyHostToDevice, s->h2d);
             }
-            if (e == cudaSuccess) e = cudaEventRecord(g->ev, s->d2h);
+            if (e == cudaSuccess) e = cudaEventRecord(s->run_ev[ri], s->h2d);
+        }
+        if (e != cudaSuccess) { fail_worker(s, e, "serve: staging copy"); return; }
+        // launch the groups in arrival order, each after the copy of its data
+        int waited = -1;
+        for (const Planned& p : plan) {
+            Group* g = p.g;
+            const int64_t total = g->e - g->b;
+            if (p.need > waited) {
+                e = cudaStreamWaitEvent(s->compute, s->run_ev[p.need], 0);
+                waited = p.need;
+            }
+            if (e != cudaSuccess) break;
+            if (g->kind == CC_OP_UPDATE) {
+                cc_status st = total ? cc_bulk_update(s->ctx, s->ring[CC_OP_UPDATE].buf + 2 * g->b, total) : CC_OK;
+                if (st != CC_OK) { fail_worker(s, cudaErrorUnknown, "serve: bulk update"); return; }
+                e = cudaEventRecord(g->ev, s->compute);
+            } else {
+                cc_status st = total ? cc_bulk_query(s->ctx, s->ring[CC_OP_QUERY].buf + 2 * g->b, total,
+                                                     s->ring_out + g->b)
+                                     : CC_OK;
+                if (st != CC_OK) { fail_worker(s, cudaErrorUnknown, "serve: bulk query"); return; }
+                e = cudaEventRecord(s->ev_q, s->compute);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s->d2h, s->ev_q, 0);
+                for (int64_t i = p.r0; i < p.r1 && e == cudaSuccess;) {  // contiguous outputs: one copy
+                    int64_t j = i + 1;
+                    int64_t pairs = batch[i].k;
+                    while (j < p.r1 && batch[j].out == batch[i].out + pairs) pairs += batch[j++].k;
+                    if (pairs > 0) {
+                        e = cudaMemcpyAsync(batch[i].out, s->ring_out + batch[i].off, (size_t)pairs,
+                                            cudaMemcpyDeviceToHost, s->d2h);
+                        if (e == cudaErrorInvalidValue && j > i + 1) {  // spans two allocations
+                            cudaGetLastError();
+                            e = cudaSuccess;
+                            for (int64_t r = i; r < j && e == cudaSuccess; r++)
+                                if (batch[r].k > 0)
+                                    e = cudaMemcpyAsync(batch[r].out, s->ring_out + batch[r].off, (size_t)batch[r].k,
+                                                        cudaMemcpyDeviceToHost, s->d2h);
+                        }
+                    }
+                    i = j;
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(g->ev, s->d2h);
+            }
+            if (e != cudaSuccess) break;
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                g->launched = true;
+                s->cv_reap.notify_one();
+            }
         }
         if (e != cudaSuccess) { fail_worker(s, e, "serve: launch"); return; }
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            g->launched = true;
-            s->cv_reap.notify_one();
-        }
     }
 }
 
@@ -343,18 +418,18 @@ cc_status cc_server_create(cc_ctx* ctx, const cc_server_config* cfg, cc_server**
     cudaError_t e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->h2d, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_q, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&s->ring, sizeof(int32_t) * 2 * (size_t)s->cap);
+    for (int kind = 0; kind < 2 && e == cudaSuccess; kind++)
+        e = cudaMalloc(&s->ring[kind].buf, sizeof(int32_t) * 2 * (size_t)s->cap);
     if (e == cudaSuccess) e = cudaMalloc(&s->ring_out, (size_t)s->cap);
     // the new streams do not wait for the handle's old stream: order them once
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->prev_stream);
     cudaSetDevice(prev);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(s->ring);
+        cudaFree(s->ring[0].buf);
+        cudaFree(s->ring[1].buf);
         cudaFree(s->ring_out);
-        if (s->ev_in) cudaEventDestroy(s->ev_in);
         if (s->ev_q) cudaEventDestroy(s->ev_q);
         if (s->compute) cudaStreamDestroy(s->compute);
         if (s->h2d) cudaStreamDestroy(s->h2d);
@@ -497,9 +572,10 @@ cc_status cc_server_destroy(cc_server* s) {
         delete g;
     }
     for (cudaEvent_t ev : s->spare_events) cudaEventDestroy(ev);
-    cudaFree(s->ring);
+    cudaFree(s->ring[0].buf);
+    cudaFree(s->ring[1].buf);
     cudaFree(s->ring_out);
-    cudaEventDestroy(s->ev_in);
+    for (cudaEvent_t ev : s->run_ev) cudaEventDestroy(ev);
     cudaEventDestroy(s->ev_q);
     cudaStreamDestroy(s->compute);
     cudaStreamDestroy(s->h2d);
