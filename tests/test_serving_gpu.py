@@ -115,6 +115,40 @@ def test_served_equals_alone(cc, mode):
         assert st["groups"] == len(reqs)
 
 
+@pytest.mark.parametrize("ring,group,merge", [(1 << 13, 1 << 11, True), (1 << 12, 1 << 9, True),
+                                              (3000, 1 << 12, False), (1 << 20, 1 << 22, True)])
+def test_contiguous_requests_share_copies(cc, ring, group, merge):
+    # the requests' data are consecutive views of one pinned edge buffer and
+    # one pinned pair buffer, and the answers consecutive views of one pinned
+    # output buffer, as in a caller that keeps its stream in one place: copies
+    # then run across requests and groups, in both rings, and wrap round the
+    # small rings; every query answers as it would alone, in arrival order
+    n, reqs, data = make_trace(scale=15, m=1 << 18, seed=12, ulo=4, uhi=10, qlo=4, qhi=10)
+    e_all = torch.cat([d for r, d in zip(reqs, data) if r.kind == 0]).pin_memory()
+    q_all = torch.cat([d for r, d in zip(reqs, data) if r.kind == 1]).pin_memory()
+    o_all = torch.zeros(q_all.shape[0], dtype=torch.uint8).pin_memory()
+    views, eo, qo = [], 0, 0
+    for r in reqs:
+        if r.kind == 0:
+            views.append((0, e_all[eo:eo + r.size], None))
+            eo += r.size
+        else:
+            views.append((1, q_all[qo:qo + r.size], o_all[qo:qo + r.size]))
+            qo += r.size
+    want, want_labels = alone_answers(n, reqs, [v[1] for v in views])
+    f = cc.Forest(n)
+    with cc.Server(f, ring_pairs=ring, max_group_pairs=group, merge=merge) as srv:
+        srv.enqueue_list(views)
+        srv.drain()
+        st = srv.stats()
+    for i, (kind, d, o) in enumerate(views):
+        if kind == 1:
+            assert np.array_equal(o.numpy(), want[i]), f"request {i}"
+    assert np.array_equal(f.labels().cpu().numpy(), want_labels)
+    assert st["completed"] == len(reqs) and st["groups"] >= (len(reqs) if not merge else 2)
+    f.sync()
+
+
 def test_empty_requests_do_not_hide_a_full_ring(cc):
     # A request of zero pairs becomes a group that sits at the ring's head
     # without occupying it. With no merging (one group per request) and a
