@@ -125,13 +125,16 @@ struct cc_ctx {
     int64_t* seg_off = nullptr;      // device copy
     int64_t cap_ops = 0;             // capacity of the table buffers, in ops
     size_t table_bytes = 0;
-    void* staging = nullptr;         // pinned host tables
+    // pinned host tables, two: the host fills one while the graph launched
+    // with the other (its copy and its kernel) may still be queued or running
+    void* staging[2] = {nullptr, nullptr};
     void* tables = nullptr;          // device tables
-    cudaEvent_t staging_free = nullptr;  // recorded after the tables were copied
-    bool staging_pending = false;
+    cudaEvent_t staging_free[2] = {nullptr, nullptr};  // recorded after the submit that used it
+    bool staging_pending[2] = {false, false};
+    int stage = 0;                   // the staging buffer the next submit fills
     cudaStream_t capture_stream = nullptr;
-    cudaGraphExec_t graph_exec = nullptr;
-    int64_t graph_key[5] = {-1, -1, -1, -1, -1};
+    cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};  // captured with staging[0] / staging[1]
+    int64_t graph_key[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};
     std::vector<int> bucket_count, op_begin_h, order_h;
     std::vector<int64_t> work_h;
 
@@ -588,10 +591,12 @@ cc_status cc_destroy(cc_ctx* c) {
             cudaEventDestroy(t.b);
         }
         for (auto ev : c->spare) cudaEventDestroy(ev);
-        if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+        for (int j = 0; j < 2; j++) {
+            if (c->graph_exec[j]) cudaGraphExecDestroy(c->graph_exec[j]);
+            if (c->staging_free[j]) cudaEventDestroy(c->staging_free[j]);
+            if (c->staging[j]) cudaFreeHost(c->staging[j]);
+        }
         if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
-        if (c->staging_free) cudaEventDestroy(c->staging_free);
-        if (c->staging) cudaFreeHost(c->staging);
         cudaFree(c->tables);
         cudaFree(c->seg_off);
         cudaFree(c->a2);
@@ -878,38 +883,44 @@ cc_status ensure_tables(cc_ctx* c, int64_t nops) {
         if (e == cudaSuccess) e = cudaMemcpy(c->seg_off, c->seg_off_h.data(), sizeof(int64_t) * 2, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(e, "cc_submit: segment offsets");
     }
-    if (!c->staging_free) {
-        cudaError_t e = cudaEventCreateWithFlags(&c->staging_free, cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(e, "cc_submit: event");
-    }
+    for (int j = 0; j < 2; j++)
+        if (!c->staging_free[j]) {
+            cudaError_t e = cudaEventCreateWithFlags(&c->staging_free[j], cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(e, "cc_submit: event");
+        }
     if (nops <= c->cap_ops) return CC_OK;
     int64_t cap = c->cap_ops ? c->cap_ops : 1024;
     while (cap < nops) cap *= 2;
-    if (c->staging_pending) {
-        cudaEventSynchronize(c->staging_free);
-        c->staging_pending = false;
-    }
+    for (int j = 0; j < 2; j++)
+        if (c->staging_pending[j]) {
+            cudaEventSynchronize(c->staging_free[j]);
+            c->staging_pending[j] = false;
+        }
     const TableLayout L = table_layout(cap, c->G);
-    void* staging = nullptr;
+    void* staging[2] = {nullptr, nullptr};
     void* tables = nullptr;
-    cudaError_t e = cudaMallocHost(&staging, L.bytes);
+    cudaError_t e = cudaMallocHost(&staging[0], L.bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&staging[1], L.bytes);
     if (e == cudaSuccess) e = cudaMalloc(&tables, L.bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (staging) cudaFreeHost(staging);
+        if (staging[0]) cudaFreeHost(staging[0]);
+        if (staging[1]) cudaFreeHost(staging[1]);
         return fail(CC_ERR_OOM, "cc_submit: table buffers of %zu bytes", L.bytes);
     }
     cudaStreamSynchronize(c->stream);  // the old tables may still be read by a running submit
-    if (c->staging) cudaFreeHost(c->staging);
+    for (int j = 0; j < 2; j++) {
+        if (c->staging[j]) cudaFreeHost(c->staging[j]);
+        c->staging[j] = staging[j];
+        if (c->graph_exec[j]) {
+            cudaGraphExecDestroy(c->graph_exec[j]);
+            c->graph_exec[j] = nullptr;
+        }
+    }
     cudaFree(c->tables);
-    c->staging = staging;
     c->tables = tables;
     c->cap_ops = cap;
     c->table_bytes = L.bytes;
-    if (c->graph_exec) {
-        cudaGraphExecDestroy(c->graph_exec);
-        c->graph_exec = nullptr;
-    }
     return CC_OK;
 }
 
@@ -941,15 +952,16 @@ cc_status cc_submit(cc_ctx* c, const cc_op* ops, int64_t nops) {
     CC_DEVICE(c);
     cc_status st = ensure_tables(c, nops);
     if (st != CC_OK) return st;
-    if (c->staging_pending) {  // the previous submit's copy must be done before refilling
-        cudaError_t e = cudaEventSynchronize(c->staging_free);
+    const int j = c->stage;
+    if (c->staging_pending[j]) {  // the submit before the previous one used this buffer
+        cudaError_t e = cudaEventSynchronize(c->staging_free[j]);
         if (e != cudaSuccess) return cuda_fail(e, "cc_submit: wait for staging");
-        c->staging_pending = false;
+        c->staging_pending[j] = false;
     }
     // bucket the operations by graph, keeping their order within a graph
     const int32_t G = c->G;
     const TableLayout L = table_layout(c->cap_ops, G);
-    char* base = static_cast<char*>(c->staging);
+    char* base = static_cast<char*>(c->staging[j]);
     cc::SegOp* sops = reinterpret_cast<cc::SegOp*>(base + L.ops);
     int* op_begin = reinterpret_cast<int*>(base + L.op_begin);
     int* order = reinterpret_cast<int*>(base + L.order);
@@ -995,10 +1007,10 @@ cc_status cc_submit(cc_ctx* c, const cc_op* ops, int64_t nops) {
     st = run(c, CC_K_SEGMENTED, "submit", [&]() -> cudaError_t {
         cudaError_t e;
         if (use_graph) {
-            if (!c->graph_exec || memcmp(key, c->graph_key, sizeof key) != 0) {
-                if (c->graph_exec) {
-                    cudaGraphExecDestroy(c->graph_exec);
-                    c->graph_exec = nullptr;
+            if (!c->graph_exec[j] || memcmp(key, c->graph_key[j], sizeof key) != 0) {
+                if (c->graph_exec[j]) {
+                    cudaGraphExecDestroy(c->graph_exec[j]);
+                    c->graph_exec[j] = nullptr;
                 }
                 e = cc::prepare_segmented(cfg);
                 if (e != cudaSuccess) return e;
@@ -1009,31 +1021,34 @@ cc_status cc_submit(cc_ctx* c, const cc_op* ops, int64_t nops) {
                 cudaGraph_t graph = nullptr;
                 e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
                 if (e != cudaSuccess) return e;
-                cudaError_t e1 = cudaMemcpyAsync(c->tables, c->staging, c->table_bytes, cudaMemcpyHostToDevice, c->capture_stream);
+                cudaError_t e1 = cudaMemcpyAsync(c->tables, c->staging[j], c->table_bytes, cudaMemcpyHostToDevice, c->capture_stream);
                 if (e1 == cudaSuccess) e1 = cudaMemsetAsync(&c->ds->queue, 0, sizeof(unsigned), c->capture_stream);
                 if (e1 == cudaSuccess) e1 = cc::launch_segmented(c->parent, c->seg_off, t, &c->ds->queue, c->ds, cfg, c->capture_stream);
                 e = cudaStreamEndCapture(c->capture_stream, &graph);
                 if (e1 != cudaSuccess) e = e1;
-                if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec[j], graph, 0);
                 if (graph) cudaGraphDestroy(graph);
                 if (e != cudaSuccess) {
-                    c->graph_exec = nullptr;
+                    c->graph_exec[j] = nullptr;
                     return e;
                 }
-                memcpy(c->graph_key, key, sizeof key);
+                memcpy(c->graph_key[j], key, sizeof key);
             }
-            e = cudaGraphLaunch(c->graph_exec, c->stream);
+            e = cudaGraphLaunch(c->graph_exec[j], c->stream);
         } else {
             e = cc::prepare_segmented(cfg);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(c->tables, c->staging, L.order + sizeof(int) * c->order_h.size(), cudaMemcpyHostToDevice, c->stream);
+                e = cudaMemcpyAsync(c->tables, c->staging[j], L.order + sizeof(int) * c->order_h.size(), cudaMemcpyHostToDevice, c->stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(&c->ds->queue, 0, sizeof(unsigned), c->stream);
             if (e == cudaSuccess) e = cc::launch_segmented(c->parent, c->seg_off, t, &c->ds->queue, c->ds, cfg, c->stream);
         }
-        if (e == cudaSuccess) e = cudaEventRecord(c->staging_free, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(c->staging_free[j], c->stream);
         return e;
     });
-    if (st == CC_OK) c->staging_pending = true;
+    if (st == CC_OK) {
+        c->staging_pending[j] = true;
+        c->stage = j ^ 1;
+    }
     c->flat = false;
     c->fresh = false;
     return st;
