@@ -122,6 +122,27 @@ def test_segmented_full_size_and_replay(cc):
     assert f.kernel_stats()["segmented"] == 2
 
 
+@pytest.mark.parametrize("opts", [{}, {"seg_graph": 0}])
+def test_consecutive_submits_without_waiting(cc, opts):
+    # one operation list cut into submits of different lengths, issued back to
+    # back with no synchronisation: the host fills one staging buffer while
+    # the previous submit (which used the other) is still queued, so the tables
+    # of every submit must reach the device intact; order within a graph is
+    # kept across the cuts, so every answer is the oracle's
+    w = I.segmented_workload(G=64, seed=6, nlo=5, nhi=12, blo=3, bhi=9)
+    f = cc.Forest.segmented(w.n, **opts)
+    ops, out, qbase, keep = build_ops(cc, w, interleave_seed=2)
+    cuts = [0, len(ops) // 7, len(ops) // 3, len(ops) // 3 + 5, (2 * len(ops)) // 3, len(ops) - 1, len(ops)]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        if b > a:
+            f.submit(ops[a:b])
+    got = out.cpu().numpy()
+    f.sync()
+    want, labels = oracle_answers(w, qbase)
+    assert np.array_equal(got, want), f"{int((got != want).sum())} answers differ"
+    assert f.kernel_stats()["segmented"] == sum(1 for a, b in zip(cuts[:-1], cuts[1:]) if b > a)
+
+
 def test_submit_errors_and_plain_ids(cc):
     w = I.segmented_workload(G=4, seed=5, nlo=4, nhi=6, blo=2, bhi=4)
     f = cc.Forest.segmented(w.n)
