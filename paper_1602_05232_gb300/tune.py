@@ -50,6 +50,10 @@ PLAIN_SPACE = {
     "hook_warp": [0, 1],
     "big_filter": [0, 384, 640, 896],
 }
+# options that only act together: the largest-component filter is built by
+# full compression passes, so it does nothing while compression is off
+PLAIN_PAIRS = (("big_filter", "compress_every"),)
+
 PLAIN_START = {"update_variant": 0, "edges_per_thread": 2, "block": 256, "compress_every": 1,
                "compress_scope": 0, "query_halving": 0, "l2_persist": 0, "query_variant": 0,
                "pdl": 1, "query_pairs_per_thread": 0, "hook": 0, "edge_order": 0, "hook_warp": 0,
@@ -96,11 +100,14 @@ def _store(workload: str, best: dict, ms: float, table: list) -> None:
 
 
 def coordinate_descent(space: dict, start, evaluate, rounds: int = 2, finalists: int = 3,
-                       log=None) -> tuple[dict, float, list]:
+                       log=None, pairs=()) -> tuple[dict, float, list]:
     """Minimise evaluate(options) over the product space by sweeping one
     parameter at a time, from one start point or from each of a list of them
     (sharing the measurements); the best few points seen are timed again and
-    the fastest wins. Returns (best options, time, [(options, time)])."""
+    the fastest wins. `pairs`: options that only act together (each (a, b) is
+    also swept over the product of their values in every round), which single
+    moves cannot find from a start where neither is on. Returns (best options,
+    time, [(options, time)])."""
     seen: dict[str, float] = {}
 
     def ev(o):
@@ -122,6 +129,13 @@ def coordinate_descent(space: dict, start, evaluate, rounds: int = 2, finalists:
                     t = ev(cand)
                     if t < best_t:
                         best, best_t, improved = cand, t, True
+            for a, b in pairs:
+                for va in space.get(a, ()):
+                    for vb in space.get(b, ()):
+                        cand = dict(best, **{a: va, b: vb})
+                        t = ev(cand)
+                        if t < best_t:
+                            best, best_t, improved = cand, t, True
             if not improved:
                 break
     table = [(json.loads(k), t) for k, t in seen.items()]
@@ -197,7 +211,8 @@ def canonical_plain(options: dict) -> dict:
 def tune_plain(stream_obj, space=PLAIN_SPACE, start=PLAIN_START, repeats: int = 3, log=None):
     """start: one option dict or a list of them (see coordinate_descent)."""
     bench = PlainBench(stream_obj)
-    best, t, table = coordinate_descent(space, start, lambda o: bench.time(o, repeats), log=log)
+    best, t, table = coordinate_descent(space, start, lambda o: bench.time(o, repeats), log=log,
+                                        pairs=PLAIN_PAIRS)
     return canonical_plain(best), t, table
 
 

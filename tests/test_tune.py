@@ -70,3 +70,19 @@ def test_canonical_plain_drops_a_filter_nothing_builds():
     assert tune.canonical_plain(o)["big_filter"] == 0
     o = {"compress_every": 6, "compress_scope": 0, "big_filter": 640}
     assert tune.canonical_plain(o) == o
+
+
+def test_coordinate_descent_pairs_find_options_that_only_act_together():
+    # b does nothing while a is 0 and a costs time while b is 0: from (0, 0)
+    # no single move improves, the joint move (2, 1) does
+    space = {"a": [0, 1, 2], "b": [0, 1], "c": [0, 1]}
+
+    def cost(o):
+        if o["a"] and o["b"]:
+            return 1.0 + 0.1 * o["c"]
+        return 3.0 + (1.0 if o["a"] else 0.0) + 0.1 * o["c"]
+
+    best, t, _ = tune.coordinate_descent(space, {"a": 0, "b": 0, "c": 0}, cost)
+    assert best == {"a": 0, "b": 0, "c": 0}
+    best, t, _ = tune.coordinate_descent(space, {"a": 0, "b": 0, "c": 0}, cost, pairs=(("a", "b"),))
+    assert best["a"] > 0 and best["b"] == 1 and t == 1.0
