@@ -595,6 +595,15 @@ PAPER_T20C = {"random": [36.87, 46.02, 60.66, 63.90], "rmat5": [26.08, 34.19, 49
 PAPER_BATCHES = [500_000, 1_000_000, 5_000_000, 10_000_000]
 
 
+def paper_compress_every(tuned_every: int, batch: int) -> int:
+    """The compression interval, in Bulk-Updates, at `batch` edges per update
+    when `tuned_every` was tuned at the largest paper batch: about as many
+    edges between two compressions. 0 (never) stays 0."""
+    if tuned_every <= 0:
+        return 0
+    return max(1, round(tuned_every * PAPER_BATCHES[-1] / batch))
+
+
 def run_paper(args, rank: int, world: int, local_rank: int, dist) -> dict:
     """Bulk-Update throughput (total edges / total update time, as in Table 3)
     on a paper-size stream at the paper's four batch sizes, and the number of
@@ -618,8 +627,7 @@ def run_paper(args, rank: int, world: int, local_rank: int, dist) -> dict:
         every = {}
         for b in PAPER_BATCHES:
             cuts = list(range(0, s0.m, b)) + [s0.m]
-            ce = int(opts.get("compress_every", 1))
-            every[b] = max(1, round(ce * PAPER_BATCHES[-1] / b)) if ce > 0 else 0
+            every[b] = paper_compress_every(int(opts.get("compress_every", 1)), b)
             f.set_option("compress_every", every[b])
 
             def one_pass():

@@ -89,3 +89,30 @@ def test_reference_arm_on_the_headline_workload():
     assert d["impl"] == "reference" and d["unit"] == "edges/s" and d["value"] > 0
     assert "8192x8192" in d["config"]["workload"] and "pass" in d["config"]["step"]
     assert d["cpu_baseline"]["value"] == d["value"]
+
+
+def test_paper_compression_interval_scales_with_the_batch():
+    # the interval tuned at the largest paper batch, kept in edges at the
+    # smaller ones; never compressing stays never
+    sys.path.insert(0, str(ROOT))
+    import bench
+    big = bench.PAPER_BATCHES[-1]
+    assert bench.paper_compress_every(6, big) == 6
+    assert bench.paper_compress_every(6, big // 20) == 120
+    assert bench.paper_compress_every(8, big // 2) == 16
+    assert bench.paper_compress_every(0, big // 20) == 0
+    assert bench.paper_compress_every(1, 2 * big) == 1          # never below one
+    for b in bench.PAPER_BATCHES:
+        e = bench.paper_compress_every(6, b)
+        assert abs(e * b - 6 * big) <= b                       # edges between compressions kept
+
+
+def test_ncu_traffic_is_withheld_under_option_overrides(monkeypatch):
+    # measured DRAM bytes belong to the tuned configuration they were taken with
+    sys.path.insert(0, str(ROOT))
+    import bench
+    monkeypatch.setattr(bench, "OPTION_OVERRIDES", {"big_filter": 0})
+    assert bench.ncu_traffic("update", "grid") == (None, None)
+    monkeypatch.setattr(bench, "OPTION_OVERRIDES", {})
+    t, k = bench.ncu_traffic("update", "grid")
+    assert t is None or (t > 0 and k)
